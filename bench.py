@@ -1,0 +1,346 @@
+"""Benchmark: grid-point-steps/s of the QG LES step on one GB300 (or N replicas).
+
+Default workload: 2048^2 island, dynamic Leith, beta = 5, U = 0.5, FP32 fields
+with FP64 Germano sums / diagnostics / low-k inversion (the production step).
+A "step" is one full time step: three RK3 stages with the dynamic
+coefficient, the viscous factor, the Brinkman and the sponge sub-steps.
+
+Prints one JSON line.  Multi-GPU (torchrun, one process per GPU) runs
+independent replicas: the step has no data-parallel split on one grid.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth as S  # noqa: E402
+
+WORKLOADS = {
+    "island2048-dleith": S.island2048_dleith,
+    "island128-smag": S.island128_smag,
+    "cape512-dleith": lambda: S.cape512(S.DLEITH),
+    "cape512-dsmag": lambda: S.cape512(S.DSMAG),
+    "cape512-smag": lambda: S.cape512(S.SMAG),
+    "cape512-leith": lambda: S.cape512(S.LEITH),
+}
+
+METRIC = "grid-pt-steps/s at 2048^2 dyn-Leith, FP32 vs FP64 at stated err; % HBM peak"
+UNIT = "grid-pt-steps/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_bytes(wl, precision_fp32: bool):
+    """Minimal HBM bytes per launch of each kernel class of one step.
+
+    Units: a mixed array holds N x (K+1) complex, a spectral array (K+1) x
+    (2K+1) complex, a physical field N x N reals; each is read or written once
+    where the algorithm needs it.  Returns {class: (launches_per_step,
+    bytes_per_launch)}.
+    """
+    n = wl.n
+    K = (n - 1) // 3
+    esz = 4 if precision_fp32 else 8
+    csz = 2 * esz
+    I = n * (K + 1) * csz
+    Sp = (K + 1) * (2 * K + 1) * csz
+    R = n * n * esz
+    kind = wl.closure
+    nin = {S.NONE: 4, S.LEITH: 4, S.SMAG: 6, S.DLEITH: 8, S.DSMAG: 12}[kind]
+    nout = {S.NONE: 1, S.LEITH: 3, S.SMAG: 3, S.DLEITH: 6, S.DSMAG: 6}[kind]
+    dyn = kind in (S.DSMAG, S.DLEITH)
+    has_mask = wl.geometry != "none"
+    has_sponge = wl.sponge
+    after = 2 if has_mask else (1 if has_sponge else nin)
+    out = {"row_stage": (3, (nin + nout) * I)}
+    # column pass of the stages: stage 0 reads w0 only; later stages w0 and ws;
+    # stages 0, 1 write ws and nin mixed arrays; stage 2 writes `after` mixed arrays
+    stage_bytes = []
+    for s in range(3):
+        b = (2 * Sp if dyn else nout * I)  # J, D (dynamic) or the forward inputs (static)
+        b += Sp if s == 0 else 2 * Sp
+        b += (Sp + nin * I) if s < 2 else after * I
+        stage_bytes.append(b)
+    out["col_stage"] = (3, sum(stage_bytes) / 3)
+    if dyn:
+        out["col_reduce"] = (3, 6 * I + 2 * Sp)
+    if has_mask:
+        out["row_brinkman"] = (1, 4 * I + R)
+        out["col_curl"] = (1, 2 * I + (I if has_sponge else Sp + nin * I))
+    if has_sponge:
+        out["row_sponge"] = (1, 2 * I + R)
+        out["col_final"] = (1, I + Sp + nin * I)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def time_oracle(wl, max_seconds: float, warmup: int = 1):
+    """The FP64 CPU oracle, as it stands, on the workload; bounded wall time."""
+    import oracle as O
+    ref = O.QGOracle(wl.n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure, c=wl.c),
+                     O.Params(dt=wl.dt, nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate))
+    ref.set_state(wl.omega0())
+    for _ in range(warmup):
+        ref.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        ref.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= max_seconds or el / steps * (steps + 1) > 1.5 * max_seconds:
+            break
+    return steps, el
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = float(os.environ.get("QG_REF_SECONDS", "60"))
+    steps, el = time_oracle(wl, budget, warmup=min(args.warmup, 1))
+    value = wl.n * wl.n * steps / el
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": steps,
+        "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} full {wl.n}^2 steps of the FP64 numpy oracle (bounded to ~{budget:.0f} s)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="island2048-dleith", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2508_06678_gb300 as qg
+    from paper_2508_06678_gb300._lib import KERNEL_CLASSES, LIB_PATH, load
+
+    if not os.path.exists(LIB_PATH):
+        from paper_2508_06678_gb300.build import build
+        build()
+    lib = load()
+    import ctypes as C
+
+    fp32 = args.precision == "fp32"
+    stream = torch.cuda.Stream()
+    solver = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32 if fp32 else qg.QG_FP64, stream=stream)
+    w0 = wl.omega0()
+    solver.set_state(w0)
+    solver.step(args.warmup)
+    solver.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- timed region: K steps on device-resident state, per-kernel events on
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    qg_h = solver.h
+    lib.qg_profile(qg_h, 1)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    counts = (C.c_int32 * 8)()
+    kms = (C.c_double * 8)()
+    lib.qg_kernel_times(qg_h, counts, kms, 8)
+    lib.qg_profile(qg_h, 0)
+    solver.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * wl.n * wl.n * args.steps / (ms / 1e3)
+    launches = int(sum(counts))
+
+    # ---- roofline of the dominant kernel class
+    peaks, peak_src = measured_peaks()
+    model = algorithmic_bytes(wl, fp32)
+    per_class = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(8)}
+    dom = max((k for k in per_class if per_class[k][0] > 0 and k in model), key=lambda k: per_class[k][1])
+    n_l, t_l = per_class[dom]
+    avg_s = t_l / n_l / 1e3
+    bytes_launch = model[dom][1]
+    achieved = bytes_launch / avg_s / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    step_bytes = sum(a * b for a, b in model.values())
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", f"traffic_{wl.name}_{args.precision}.json")
+    if os.path.exists(prof_path):
+        try:
+            rec = json.load(open(prof_path))
+            if rec.get("kernel_class") == dom:
+                traffic = rec.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_src,
+                "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
+                "step_model_bytes": step_bytes,
+                "step_frac": step_bytes / (ms / 1e3 / args.steps) / 1e9 / peak}
+
+    # ---- end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    host_in = torch.from_numpy(w0.astype(np.float32 if fp32 else np.float64)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dtype_code = qg.QG_FP32 if fp32 else qg.QG_FP64
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lib.qg_set_state(qg_h, C.c_void_p(host_in.data_ptr()), 0, dtype_code)
+    lib.qg_step(qg_h, args.steps)
+    lib.qg_get_state(qg_h, C.c_void_p(host_out.data_ptr()), 0, dtype_code)
+    diag = solver.diagnostics(raise_nonfinite=False)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    esz = 4 if fp32 else 8
+    e2e = {"value": world * wl.n * wl.n * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": wl.n * wl.n * esz / args.steps,
+           "d2h_bytes_per_step": (wl.n * wl.n * esz + 56) / args.steps,
+           "api": "qg_set_state(host) + qg_step(K) + qg_get_state(host) + qg_diagnostics"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            steps_c, el_c = time_oracle(wl, args.cpu_seconds, warmup=0)
+            cpu = {"value": wl.n * wl.n * steps_c / el_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{steps_c} full {wl.n}^2 step(s) of the FP64 numpy oracle (single-threaded), "
+                             f"{el_c:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure],
+                       "geometry": wl.geometry, "beta": wl.beta, "U": wl.U, "dt": wl.dt,
+                       "precision": args.precision + (" (FP64 Germano sums, diagnostics, low-k inversion)"
+                                                      if fp32 else ""),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "working set > 126 MB L2 (inputs larger than L2, no flush)",
+                       "final_energy": diag["energy"], "final_coeff": diag["coeff"], "finite": diag["finite"]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "kernel_ms": {k: v[1] for k, v in per_class.items() if v[0]},
+            "kernel_launches": {k: v[0] for k, v in per_class.items() if v[0]},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

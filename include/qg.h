@@ -1,0 +1,190 @@
+/*
+ * qg.h -- C-ABI of libqg: one time step of the forced-dissipative barotropic
+ * quasi-geostrophic beta-plane vorticity equation with LES closures, Brinkman
+ * volume penalisation and an inflow sponge, on one GB300 GPU (sm_103a).
+ *
+ * Model (Sec. II-A, Eq. 1):
+ *     dw/dt + J(psi, w) = nu lap(w) - mu w - beta dpsi/dx + F_obs + F_sponge + Pi
+ *     (u, v) = (-dpsi/dy, dpsi/dx),  w = lap(psi),
+ * with a uniform inflow U added to the zeroth Fourier mode of u (Sec. II-D),
+ * F_obs = -curl(chi_obs u / eta) (Eq. 2, u_obs = 0), F_sponge =
+ * -rate chi_sponge (w - 0) (Eq. 3), and Pi = div(nu_e grad w) (Eq. 9) from one
+ * of four closures: Smagorinsky (Eq. 10), Leith (Eq. 13) and their dynamic
+ * Germano/Lilly variants (Eq. 11-12, 14).
+ *
+ * Discretisation (Sec. II-C): Fourier pseudo-spectral on an N x N doubly
+ * periodic grid of [0, L)^2, products by collocation with the 2/3 rule
+ * (square truncation |m_x|, |m_y| <= K = floor((N-1)/3)).  One step is the
+ * Lie-Trotter split of Sec. II-E with these sub-step integrators:
+ *   1. three SSP-RK3 (Shu-Osher) stages of L(w) = -J - beta v + C div(g grad w);
+ *      a dynamic C is recomputed from every stage's field;
+ *   2. the exact viscous/friction factor exp(-(nu |k|^2 + mu) dt);
+ *   3. the exact Brinkman sub-step: total velocity times exp(-chi dt / eta),
+ *      then w = T curl(u);
+ *   4. the exact sponge sub-step: w times exp(-rate chi_s dt), then T;
+ *   5. the mean mode set to zero.
+ *
+ * Conventions.  Physical arrays are row-major [y][x] (x fastest), x_i = i L/N.
+ * Every call returns QG_OK (0) or a negative QG_ERR_* code and never throws;
+ * qg_last_error() returns a thread-local message for the last failure.  Host
+ * arrays passed in are copied before the call returns; device pointers
+ * (on_device = 1) are borrowed for the duration of the call only.  The
+ * library allocates and owns every device buffer it uses.  Work is enqueued
+ * on the stream given at creation (NULL = the legacy default stream).
+ */
+#ifndef QG_H
+#define QG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define QG_OK 0
+#define QG_ERR_ARG (-1)       /* invalid argument: sizes, kinds, NULL pointers */
+#define QG_ERR_CUDA (-2)      /* a CUDA runtime call failed (message has the CUDA error) */
+#define QG_ERR_NONFINITE (-3) /* a non-finite value appeared in the state; stepping stopped */
+#define QG_ERR_OOM (-4)       /* device allocation failed */
+#define QG_ERR_TIMEOUT (-5)   /* reserved: a bounded device wait gave up */
+#define QG_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve (e.g. shared memory) */
+
+/* Working precision of the device fields. */
+#define QG_FP64 0
+#define QG_FP32 1
+
+/* Closure kinds (Sec. III-A). */
+#define QG_NONE 0
+#define QG_SMAG 1   /* nu_e = (c_S Delta)^2 |S|,           Eq. 10 */
+#define QG_LEITH 2  /* nu_e = (c_L Delta)^3 |grad w|,      Eq. 13 */
+#define QG_DSMAG 3  /* (c_S Delta)^2 = <HM>/<MM>,          Eq. 11-12 */
+#define QG_DLEITH 4 /* (c_L Delta)^3 = <HM>/<MM>,          Eq. 14 */
+
+/* Grid: N even, N = 2^a 3^b, 16 <= N <= 4096; L > 0; precision QG_FP32/QG_FP64. */
+typedef struct {
+  int32_t n;
+  int32_t precision;
+  double L;
+} qg_grid;
+
+/* Closure: kind, the static constant c (c_S or c_L; ignored by dynamic
+ * kinds) and the test-filter width ratio r = Delta~/Delta (2 in the paper,
+ * Sec. III-A).  The test filter is sharp and radial: |m| <= N / (2 r). */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  double c;
+  double test_ratio;
+} qg_closure;
+
+/* Time-step parameters: dt, viscosity nu = 1/Re, bottom friction mu,
+ * porosity eta of the Brinkman term (Eq. 2) and sponge rate = 1/eta_sponge
+ * (Eq. 3). */
+typedef struct {
+  double dt, nu, mu, eta, sponge_rate;
+} qg_params;
+
+/* Diagnostics of the current state.  energy = <|u'|^2>/2 of the perturbation
+ * velocity, enstrophy = <w^2>/2 (both FP64 Parseval sums), coeff = the
+ * closure coefficient C used in the last RK stage ((c Delta)^p), max_abs_omega
+ * and finite from the physical field. */
+typedef struct {
+  double t, energy, enstrophy, coeff, max_abs_omega;
+  int64_t step;
+  int32_t finite;
+  int32_t reserved;
+} qg_diag;
+
+typedef struct qg_handle qg_handle;
+
+/* Create a solver on the current CUDA device.
+ *   grid, closure, params: as above (copied).
+ *   beta: the beta-plane parameter of Eq. 1;  U: uniform inflow along +x.
+ *   mask:   chi_obs, N*N host doubles in [0, 1], or NULL for no obstacle.
+ *   sponge: chi_sponge, N*N host doubles in [0, 1], or NULL for no sponge.
+ *   cuda_stream: a cudaStream_t (as void*) all work is enqueued on.
+ *   out: receives the handle.
+ * The state starts at w = 0.  Errors: QG_ERR_ARG (bad sizes/kinds),
+ * QG_ERR_UNSUPPORTED (the grid does not fit the kernels' shared memory),
+ * QG_ERR_OOM, QG_ERR_CUDA. */
+int qg_create(const qg_grid* grid, double beta, double U, const double* mask, const double* sponge,
+              const qg_closure* closure, const qg_params* params, void* cuda_stream, qg_handle** out);
+
+/* Set the state from a physical vorticity field of N*N values (dtype QG_FP64
+ * = double, QG_FP32 = float; host if on_device = 0, device otherwise).  The
+ * field is projected: w_hat = T F[w] with the mean mode removed (Sec. II-C,
+ * II-D).  Resets the non-finite flag; keeps t and step. */
+int qg_set_state(qg_handle* h, const void* omega, int32_t on_device, int32_t dtype);
+
+/* Write the physical vorticity of the current state (N*N, dtype as above).
+ * Synchronises the handle's stream when omega is a host buffer. */
+int qg_get_state(qg_handle* h, void* omega, int32_t on_device, int32_t dtype);
+
+/* Enqueue nsteps >= 0 steps (asynchronous).  Returns QG_ERR_NONFINITE without
+ * enqueueing if an earlier step is already known to have produced a
+ * non-finite value (kernels also stop by themselves once the device flag is
+ * set).  Use qg_sync to wait and collect the status. */
+int qg_step(qg_handle* h, int32_t nsteps);
+
+/* Wait for all enqueued work; QG_ERR_NONFINITE if the state became non-finite. */
+int qg_sync(qg_handle* h);
+
+/* Synchronise and fill out (see qg_diag).  Returns QG_ERR_NONFINITE (with
+ * out filled, finite = 0) if the state is not finite. */
+int qg_diagnostics(qg_handle* h, qg_diag* out);
+
+/* Release every device buffer of the handle (NULL is ignored). */
+void qg_destroy(qg_handle* h);
+
+/* A priori SGS analysis (Sec. III, Eq. 5-8, 15) of one fully resolved field.
+ *   omega_fr: N_fr*N_fr host doubles (projected onto the 2/3 band first).
+ *   n_fr, n_les: grid sizes, n_les <= n_fr, both valid grid sizes.
+ *   mask_fr, sponge_fr: chi_obs, chi_sponge on the fine grid (NULL = absent).
+ *   closure: the closure whose Pi model is correlated with the exact Pi.
+ *   params: eta and sponge_rate enter F_obs and F_sponge (dt, nu, mu unused).
+ *   U, beta: inflow and beta (beta does not enter Pi, its term is linear).
+ *   flags: bit 0 set = omit the Gaussian factor of the grid filter.
+ *   pi_exact, pi_model: n_les*n_les host doubles (output).
+ *   pi_parts: 3*n_les*n_les host doubles (Jacobian, obstacle, sponge parts of
+ *             Eq. 8), or NULL.
+ *   pcc: receives PCC(pi_exact, pi_model) (NaN if the model term is zero).
+ * Grid filter: exp(-k^2 Delta_FF^2 / 6) times the cut-off |k| <= pi/Delta_FF,
+ * Delta_FF = L / n_les, then a spectral copy to the n_les grid.  Runs in FP64
+ * on the current device; synchronous. */
+int qg_sgs_apriori(const double* omega_fr, int32_t n_fr, int32_t n_les, double L, const double* mask_fr,
+                   const double* sponge_fr, const qg_closure* closure, const qg_params* params, double U,
+                   double beta, int32_t flags, double* pi_exact, double* pi_model, double* pi_parts, double* pcc);
+
+/* Kernel classes reported by qg_kernel_times. */
+#define QG_K_ROW_STAGE 0   /* row pass of an RK stage (products of Eq. 1, 9-14) */
+#define QG_K_COL_REDUCE 1  /* column pass: Germano partial sums (Eq. 12, 14) */
+#define QG_K_COL_STAGE 2   /* column pass: RK combine + next stage's fields */
+#define QG_K_ROW_BRINK 3   /* row pass of the Brinkman sub-step (Eq. 2) */
+#define QG_K_COL_CURL 4    /* column pass: Brinkman curl */
+#define QG_K_ROW_SPONGE 5  /* row pass of the sponge sub-step (Eq. 3) */
+#define QG_K_COL_FINAL 6   /* column pass: projection of w^{n+1}, stage-1 fields */
+#define QG_K_OTHER 7       /* state I/O and diagnostics */
+#define QG_NUM_KCLASS 8
+
+/* Tracing.  enable = 1 clears the counters and starts recording a CUDA event
+ * pair around every kernel launch on the handle's stream; 0 stops recording.
+ * Launch counts are kept whether or not recording is on. */
+int qg_profile(qg_handle* h, int32_t enable);
+
+/* Per kernel class (index QG_K_*): counts[i] = launches since the last
+ * qg_profile(h, 1) (or creation), ms[i] = summed device time of the recorded
+ * launches.  Synchronises the handle's stream.  nclass <= QG_NUM_KCLASS. */
+int qg_kernel_times(qg_handle* h, int32_t* counts, double* ms, int32_t nclass);
+
+/* Thread-local description of the last error (never NULL). */
+const char* qg_last_error(void);
+
+/* Library version string. */
+const char* qg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QG_H */

@@ -1,0 +1,769 @@
+// Host side of libqg: the C-ABI declared in include/qg.h.
+//
+// One step (Sec. II-E split, sub-step integrators as documented in qg.h) is
+// a chain of alternating row and column passes on the handle's stream:
+//
+//   for each of the 3 RK stages:
+//     row pass   : inverse x-FFT of the stage's derived fields, products, forward x-FFT
+//     column pass: forward y-FFT, L = -J - beta v + C D, RK combine, derived
+//                  fields of the next stage (or of the Brinkman/sponge sub-step),
+//                  inverse y-FFT
+//     (dynamic closures split the column pass in two around the Germano sums)
+//   Brinkman: row pass scales (u_total, v) by exp(-chi dt/eta); column pass curls
+//   sponge  : row pass scales w by exp(-rate chi_s dt); column pass projects,
+//             stores w^{n+1} and derives stage 1 of the next step.
+//
+// The column pass of one step therefore also prepares the next step, and a
+// step costs 2 + 2 x 3 (+1 per stage for dynamic closures) launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qg.h"
+#include "qg_kernels.h"
+
+using namespace qg;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
+              cudaGetErrorString(e));
+}
+
+#define CK(call, what)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool valid_n(int n) {
+  if (n < 16 || n > 4096 || (n & 1)) return false;
+  int m = n;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+FftPlan make_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  int m = n;
+  while (m % 8 == 0) { p.radix[p.npass++] = 8; m /= 8; }
+  if (m % 4 == 0) { p.radix[p.npass++] = 4; m /= 4; }
+  if (m % 2 == 0) { p.radix[p.npass++] = 2; m /= 2; }
+  while (m % 3 == 0) { p.radix[p.npass++] = 3; m /= 3; }
+  return p;
+}
+
+int max_items(int R) { return R == 3 ? 2 : 8 / R; }
+
+int threads_for(const FftPlan& p, int B, int floor_threads) {
+  int need = floor_threads;
+  for (int s = 0; s < p.npass; ++s) {
+    const int R = p.radix[s];
+    const int items = (p.n / R) * B;
+    const int t = (items + max_items(R) - 1) / max_items(R);
+    if (t > need) need = t;
+  }
+  return (need + 31) / 32 * 32;
+}
+
+// cos and sin of 2 pi j / n with the argument reduced exactly to [0, pi/4].
+void cos_sin_frac(long j, long n, double* c, double* s) {
+  j %= n;
+  if (j < 0) j += n;
+  const long q4 = 4 * j;
+  const long quad = q4 / n;
+  const long rem = q4 - quad * n;  // angle within the quadrant = (pi/2) rem / n
+  double cc, ss;
+  if (2 * rem <= n) {
+    const double phi = (M_PI / 2) * double(rem) / double(n);
+    cc = std::cos(phi);
+    ss = std::sin(phi);
+  } else {
+    const double phi = (M_PI / 2) * double(n - rem) / double(n);
+    cc = std::sin(phi);
+    ss = std::cos(phi);
+  }
+  switch (quad) {
+    case 0: *c = cc; *s = ss; break;
+    case 1: *c = -ss; *s = cc; break;
+    case 2: *c = -cc; *s = -ss; break;
+    default: *c = ss; *s = -cc; break;
+  }
+}
+
+}  // namespace
+
+struct qg_handle {
+  Geom g{};
+  int fp32 = 0;
+  size_t esz = 8;  // bytes per real
+  double L = 0, beta = 0, U = 0;
+  qg_closure cl{};
+  qg_params par{};
+  cudaStream_t stream = nullptr;
+  FftPlan plan{};
+  int W = 4, col_threads = 256, row_threads = 256;
+  size_t col_smem = 0, row_smem = 0;
+  int ncolblk = 0;
+  bool dynamic = false;
+  double static_coeff = 0.0;
+  // stage program
+  int row_prog = RP_NONE, nin = 4, nout = 1;
+  unsigned dx_mask = 0;
+  int nder = 4;
+  int der[kMaxDer] = {};
+  // device buffers
+  void* w0 = nullptr;
+  void* ws = nullptr;
+  void* jh = nullptr;
+  void* dh = nullptr;
+  void* X[kMaxIn] = {};
+  void* Y[kMaxOut] = {};
+  void* fac_b = nullptr;
+  void* fac_s = nullptr;
+  void* tw = nullptr;
+  void* visc_x = nullptr;
+  void* visc_y = nullptr;
+  void* phys = nullptr;
+  double visc_mu = 1.0;
+  double* partials = nullptr;  // Germano partial sums (2 per column block)
+  double* red = nullptr;       // diagnostics partials
+  double* dev_scalars = nullptr;  // [0..2] C per stage, [4..7] diagnostics
+  int* flag = nullptr;
+  int* flag_host = nullptr;
+  cudaEvent_t flag_event = nullptr;
+  bool flag_pending = false;
+  int64_t step = 0;
+  double t = 0;
+  std::vector<void*> allocs;
+  // tracing
+  bool prof = false;
+  int32_t launches[QG_NUM_KCLASS] = {};
+  double prof_ms[QG_NUM_KCLASS] = {};
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+
+  ~qg_handle() {
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (flag_host) cudaFreeHost(flag_host);
+    if (flag_event) cudaEventDestroy(flag_event);
+  }
+};
+
+namespace {
+
+int dalloc(qg_handle* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  h->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  return QG_OK;
+}
+
+// upload host doubles as the handle's working precision
+int upload_real(qg_handle* h, void* dst, const std::vector<double>& v) {
+  if (h->fp32) {
+    std::vector<float> f(v.begin(), v.end());
+    CK(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->stream), "upload");
+    CK(cudaStreamSynchronize(h->stream), "upload sync");
+  } else {
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+    CK(cudaStreamSynchronize(h->stream), "upload sync");
+  }
+  return QG_OK;
+}
+
+cudaEvent_t take_event(qg_handle* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// launch bracket: count, and with tracing on record an event pair around the launch
+struct Bracket {
+  qg_handle* h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Bracket(qg_handle* h_, int c) : h(h_), cls(c) {
+    h->launches[cls] += 1;
+    if (h->prof) {
+      a = take_event(h);
+      if (a) cudaEventRecord(a, h->stream);
+    }
+  }
+  void done() {
+    if (!a) return;
+    cudaEvent_t b = take_event(h);
+    if (b) {
+      cudaEventRecord(b, h->stream);
+      h->recs.push_back({cls, a, b});
+    } else {
+      h->pool.push_back(a);
+    }
+  }
+};
+
+int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
+  d.flag = use_flag ? h->flag : nullptr;
+  Bracket br(h, cls);
+  cudaError_t e = h->fp32 ? launch_row<float>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream)
+                          : launch_row<double>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream);
+  br.done();
+  if (e != cudaSuccess) return cuda_fail(e, "row pass launch");
+  return QG_OK;
+}
+
+int run_col(qg_handle* h, ColDesc& d, int cls, bool use_flag = true) {
+  d.flag = use_flag ? h->flag : nullptr;
+  Bracket br(h, cls);
+  cudaError_t e = h->fp32 ? launch_col<float>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream)
+                          : launch_col<double>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream);
+  br.done();
+  if (e != cudaSuccess) return cuda_fail(e, "column pass launch");
+  return QG_OK;
+}
+
+ColDesc col_base(qg_handle* h) {
+  ColDesc d{};
+  d.w0 = h->w0;
+  d.ws = h->ws;
+  d.jh = h->jh;
+  d.dh = h->dh;
+  d.dt = h->par.dt;
+  d.beta = h->beta;
+  d.U = h->U;
+  d.coeff = h->static_coeff;
+  d.test_ratio = h->cl.test_ratio;
+  const int p = (h->cl.kind == QG_SMAG || h->cl.kind == QG_DSMAG) ? 2 : 3;
+  d.closure_pow = p;
+  d.rpow = std::pow(h->cl.test_ratio, p);
+  d.partials = h->partials;
+  d.npartials = h->ncolblk;
+  d.visc_x = h->visc_x;
+  d.visc_y = h->visc_y;
+  d.visc_mu = h->visc_mu;
+  return d;
+}
+
+void set_stage_derived(qg_handle* h, ColDesc& d) {
+  d.nder = h->nder;
+  for (int i = 0; i < h->nder; ++i) {
+    d.der[i] = h->der[i];
+    d.dout[i] = h->X[i];
+  }
+}
+
+void set_final(qg_handle* h, ColDesc& d) {
+  d.zero_mean = 1;
+  d.store_w0 = 1;
+  set_stage_derived(h, d);
+}
+
+// after the RK combine of stage 3 (viscous factor applied): derive what the
+// next sub-step needs
+void set_after_rk(qg_handle* h, ColDesc& d) {
+  if (h->fac_b) {
+    d.nder = 2;
+    d.der[0] = D_U;
+    d.der[1] = D_V;
+    d.dout[0] = h->X[0];
+    d.dout[1] = h->X[1];
+  } else if (h->fac_s) {
+    d.nder = 1;
+    d.der[0] = D_W;
+    d.dout[0] = h->X[0];
+  } else {
+    set_final(h, d);
+  }
+}
+
+const double kRK[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+
+int enqueue_step(qg_handle* h) {
+  int rc;
+  for (int s = 0; s < 3; ++s) {
+    RowDesc r{};
+    r.prog = h->row_prog;
+    r.nin = h->nin;
+    r.nout = h->nout;
+    r.dx_mask = h->dx_mask;
+    r.check_finite = 1;
+    for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
+    for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
+    if ((rc = run_row(h, r, QG_K_ROW_STAGE))) return rc;
+
+    ColDesc c = col_base(h);
+    c.a = kRK[s][0];
+    c.b = kRK[s][1];
+    c.use_ws = s > 0;
+    if (h->dynamic) {
+      ColDesc cr = c;
+      cr.op = CO_DYN_REDUCE;
+      cr.nfwd = 6;
+      for (int i = 0; i < 6; ++i) cr.fin[i] = h->Y[i];
+      if ((rc = run_col(h, cr, QG_K_COL_REDUCE))) return rc;
+      c.op = CO_DYN_COMBINE;
+      c.nfwd = 0;
+      c.coeff_out = h->dev_scalars + s;
+    } else {
+      c.op = CO_STAGE_STATIC;
+      c.nfwd = h->nout;
+      for (int i = 0; i < h->nout; ++i) c.fin[i] = h->Y[i];
+    }
+    if (s < 2) {
+      c.store_ws = 1;
+      set_stage_derived(h, c);
+    } else {
+      c.viscous = 1;
+      set_after_rk(h, c);
+    }
+    if ((rc = run_col(h, c, (s == 2 && !h->fac_b && !h->fac_s) ? QG_K_COL_FINAL : QG_K_COL_STAGE))) return rc;
+  }
+  if (h->fac_b) {
+    RowDesc r{};
+    r.prog = RP_SCALE;
+    r.nin = r.nout = 2;
+    r.in[0] = h->X[0];
+    r.in[1] = h->X[1];
+    r.out[0] = h->Y[0];
+    r.out[1] = h->Y[1];
+    r.factor = h->fac_b;
+    r.check_finite = 1;
+    if ((rc = run_row(h, r, QG_K_ROW_BRINK))) return rc;
+    ColDesc c = col_base(h);
+    c.op = CO_CURL;
+    c.nfwd = 2;
+    c.fin[0] = h->Y[0];
+    c.fin[1] = h->Y[1];
+    if (h->fac_s) {
+      c.nder = 1;
+      c.der[0] = D_W;
+      c.dout[0] = h->X[0];
+    } else {
+      set_final(h, c);
+    }
+    if ((rc = run_col(h, c, h->fac_s ? QG_K_COL_CURL : QG_K_COL_FINAL))) return rc;
+  }
+  if (h->fac_s) {
+    RowDesc r{};
+    r.prog = RP_SCALE;
+    r.nin = r.nout = 1;
+    r.in[0] = h->X[0];
+    r.out[0] = h->Y[0];
+    r.factor = h->fac_s;
+    r.check_finite = 1;
+    if ((rc = run_row(h, r, QG_K_ROW_SPONGE))) return rc;
+    ColDesc c = col_base(h);
+    c.op = CO_FORWARD;
+    c.nfwd = 1;
+    c.fin[0] = h->Y[0];
+    set_final(h, c);
+    if ((rc = run_col(h, c, QG_K_COL_FINAL))) return rc;
+  }
+  h->step += 1;
+  h->t += h->par.dt;
+  return QG_OK;
+}
+
+// physical field of the state into h->phys (working precision)
+int state_to_phys(qg_handle* h) {
+  ColDesc c = col_base(h);
+  c.op = CO_DERIVE;
+  c.nder = 1;
+  c.der[0] = D_W;
+  c.dout[0] = h->Y[0];
+  int rc = run_col(h, c, QG_K_OTHER, false);
+  if (rc) return rc;
+  RowDesc r{};
+  r.prog = RP_COPY;
+  r.nin = 1;
+  r.nout = 1;
+  r.in[0] = h->Y[0];
+  r.out_phys = 1;
+  r.phys_out = h->phys;
+  return run_row(h, r, QG_K_OTHER, false);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qg_last_error(void) { return g_err.c_str(); }
+
+const char* qg_version(void) { return "libqg 0.1 (sm_103a)"; }
+
+int qg_create(const qg_grid* grid, double beta, double U, const double* mask, const double* sponge,
+              const qg_closure* closure, const qg_params* params, void* cuda_stream, qg_handle** out) {
+  if (!grid || !closure || !params || !out) return fail(QG_ERR_ARG, "qg_create: NULL argument");
+  *out = nullptr;
+  const int n = grid->n;
+  if (!valid_n(n)) return fail(QG_ERR_ARG, "qg_create: n=%d must be even, 2^a 3^b, 16..4096", n);
+  if (!(grid->L > 0) || !std::isfinite(grid->L)) return fail(QG_ERR_ARG, "qg_create: L must be positive");
+  if (grid->precision != QG_FP32 && grid->precision != QG_FP64)
+    return fail(QG_ERR_ARG, "qg_create: precision must be QG_FP32 or QG_FP64");
+  if (closure->kind < QG_NONE || closure->kind > QG_DLEITH) return fail(QG_ERR_ARG, "qg_create: bad closure kind");
+  if ((closure->kind == QG_DSMAG || closure->kind == QG_DLEITH) && !(closure->test_ratio > 1.0))
+    return fail(QG_ERR_ARG, "qg_create: test_ratio must exceed 1");
+  if (!(params->dt > 0) || params->nu < 0 || params->mu < 0 || (mask && !(params->eta > 0)) ||
+      (sponge && params->sponge_rate < 0))
+    return fail(QG_ERR_ARG, "qg_create: bad time-step parameters");
+
+  qg_handle* h = new qg_handle();
+  h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->fp32 = grid->precision == QG_FP32;
+  h->esz = h->fp32 ? 4 : 8;
+  h->L = grid->L;
+  h->beta = beta;
+  h->U = U;
+  h->cl = *closure;
+  h->par = *params;
+  h->dynamic = closure->kind == QG_DSMAG || closure->kind == QG_DLEITH;
+  const double delta = grid->L / n;
+  if (closure->kind == QG_SMAG) h->static_coeff = std::pow(closure->c * delta, 2);
+  if (closure->kind == QG_LEITH) h->static_coeff = std::pow(closure->c * delta, 3);
+
+  Geom& g = h->g;
+  g.n = n;
+  g.K = (n - 1) / 3;
+  g.Kc = g.K + 1;
+  g.Ny = 2 * g.K + 1;
+  g.SP = (g.Ny + 3) / 4 * 4;
+  g.kscale = 2.0 * M_PI / grid->L;
+  h->plan = make_plan(n);
+
+  int dev = 0, smem_optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "qg_create: device query");
+  }
+  const size_t csz = 2 * h->esz;
+  const size_t smem_cap = (size_t)smem_optin - 1024;
+
+  // stage program of the closure
+  static const int base4[4] = {D_U, D_V, D_WX, D_WY};
+  int nd = 0;
+  for (int i = 0; i < 4; ++i) h->der[nd++] = base4[i];
+  switch (closure->kind) {
+    case QG_NONE: h->row_prog = RP_NONE; h->nout = 1; h->dx_mask = 0; break;
+    case QG_LEITH: h->row_prog = RP_LEITH; h->nout = 3; h->dx_mask = 0x2; break;
+    case QG_SMAG:
+      h->row_prog = RP_SMAG; h->nout = 3; h->dx_mask = 0x2;
+      h->der[nd++] = D_PXY; h->der[nd++] = D_PD;
+      break;
+    case QG_DLEITH:
+      h->row_prog = RP_DLEITH; h->nout = 6; h->dx_mask = 0x12;
+      for (int i = 0; i < 4; ++i) h->der[nd++] = base4[i] | D_TEST;
+      break;
+    case QG_DSMAG:
+      h->row_prog = RP_DSMAG; h->nout = 6; h->dx_mask = 0x12;
+      h->der[nd++] = D_PXY; h->der[nd++] = D_PD;
+      for (int i = 0; i < 4; ++i) h->der[nd++] = base4[i] | D_TEST;
+      h->der[nd++] = D_PXY | D_TEST; h->der[nd++] = D_PD | D_TEST;
+      break;
+  }
+  h->nder = nd;
+  h->nin = nd;
+
+  // column tile width: 32-byte row segments, enough threads, shared memory fits
+  int W = h->fp32 ? 4 : 2;
+  const int col_max_threads = h->fp32 ? 1024 : 512;  // the kernels' launch bounds
+  for (;; W /= 2) {
+    const size_t sm = (size_t)n * W * csz + 2 * (size_t)W * g.Ny * csz;
+    const int th = threads_for(h->plan, W, 128);
+    if ((sm <= smem_cap && th <= col_max_threads) || W == 1) {
+      h->W = W;
+      h->col_smem = sm;
+      h->col_threads = th;
+      break;
+    }
+  }
+  if (h->col_smem > smem_cap || h->col_threads > col_max_threads) {
+    delete h;
+    return fail(QG_ERR_UNSUPPORTED, "qg_create: column pass does not fit (n=%d)", n);
+  }
+  const int nslot = h->nin > 2 ? h->nin : 2;
+  h->row_smem = (size_t)n * csz + (size_t)nslot * n * h->esz;
+  h->row_threads = threads_for(h->plan, 1, 256);
+  if (h->row_smem > smem_cap || h->row_threads > 512) {
+    delete h;
+    return fail(QG_ERR_UNSUPPORTED, "qg_create: row pass needs %zu B of shared memory (n=%d, closure %d)",
+                h->row_smem, n, closure->kind);
+  }
+  g.Kcp = (g.Kc + h->W - 1) / h->W * h->W;
+  g.IP = g.Kcp;
+  h->ncolblk = g.Kcp / h->W;
+
+  int rc = QG_OK;
+  const size_t spec_bytes = (size_t)g.Kcp * g.SP * csz;
+  const size_t mixed_bytes = (size_t)n * g.IP * csz;
+  const size_t phys_bytes = (size_t)n * n * h->esz;
+  if (!rc) rc = dalloc(h, &h->w0, spec_bytes);
+  if (!rc) rc = dalloc(h, &h->ws, spec_bytes);
+  if (!rc && h->dynamic) rc = dalloc(h, &h->jh, spec_bytes);
+  if (!rc && h->dynamic) rc = dalloc(h, &h->dh, spec_bytes);
+  for (int i = 0; i < h->nin && !rc; ++i) rc = dalloc(h, &h->X[i], mixed_bytes);
+  const int ny = h->nout > 2 ? h->nout : 2;
+  for (int i = 0; i < ny && !rc; ++i) rc = dalloc(h, &h->Y[i], mixed_bytes);
+  if (!rc) rc = dalloc(h, &h->phys, phys_bytes);
+  if (!rc) rc = dalloc(h, &h->tw, (size_t)n * csz);
+  if (!rc) rc = dalloc(h, &h->visc_x, (size_t)g.Kcp * h->esz);
+  if (!rc) rc = dalloc(h, &h->visc_y, (size_t)g.SP * h->esz);
+  if (!rc) rc = dalloc(h, (void**)&h->partials, (size_t)2 * h->ncolblk * sizeof(double));
+  if (!rc) rc = dalloc(h, (void**)&h->red, (size_t)2 * 1024 * sizeof(double));
+  if (!rc) rc = dalloc(h, (void**)&h->dev_scalars, 16 * sizeof(double));
+  if (!rc) rc = dalloc(h, (void**)&h->flag, sizeof(int));
+  if (!rc && mask) rc = dalloc(h, &h->fac_b, phys_bytes);
+  if (!rc && sponge) rc = dalloc(h, &h->fac_s, phys_bytes);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  e = cudaMallocHost((void**)&h->flag_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->flag_event, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "qg_create: host flag");
+  }
+  *h->flag_host = 0;
+
+  // twiddles exp(-2 pi i j / n)
+  {
+    std::vector<double> tw(2 * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+      double c, s;
+      cos_sin_frac(j, n, &c, &s);
+      tw[2 * j] = c;
+      tw[2 * j + 1] = -s;
+    }
+    if ((rc = upload_real(h, h->tw, tw))) { delete h; return rc; }
+  }
+  // exact viscous factors, separable in k_x and k_y
+  {
+    const double nu = params->nu, dt = params->dt;
+    std::vector<double> vx(g.Kcp, 0.0), vy(g.SP, 0.0);
+    for (int m = 0; m < g.Kcp; ++m) {
+      const double k = g.kscale * m;
+      vx[m] = std::exp(-nu * k * k * dt);
+    }
+    for (int r = 0; r < g.Ny; ++r) {
+      const double k = g.kscale * my_of_r(g, r);
+      vy[r] = std::exp(-nu * k * k * dt);
+    }
+    h->visc_mu = std::exp(-params->mu * dt);
+    if ((rc = upload_real(h, h->visc_x, vx)) || (rc = upload_real(h, h->visc_y, vy))) { delete h; return rc; }
+  }
+  // exact penalisation factors
+  if (mask) {
+    std::vector<double> f((size_t)n * n);
+    for (size_t i = 0; i < f.size(); ++i) f[i] = std::exp(-mask[i] * params->dt / params->eta);
+    if ((rc = upload_real(h, h->fac_b, f))) { delete h; return rc; }
+  }
+  if (sponge) {
+    std::vector<double> f((size_t)n * n);
+    for (size_t i = 0; i < f.size(); ++i) f[i] = std::exp(-params->sponge_rate * sponge[i] * params->dt);
+    if ((rc = upload_real(h, h->fac_s, f))) { delete h; return rc; }
+  }
+  // the zero state derives to zero fields: X already zeroed
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "qg_create: sync");
+  }
+  *out = h;
+  return QG_OK;
+}
+
+void qg_destroy(qg_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+int qg_set_state(qg_handle* h, const void* omega, int32_t on_device, int32_t dtype) {
+  if (!h || !omega) return fail(QG_ERR_ARG, "qg_set_state: NULL argument");
+  if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_set_state: bad dtype");
+  const size_t count = (size_t)h->g.n * h->g.n;
+  const int src32 = dtype == QG_FP32;
+  if (on_device) {
+    CK(launch_convert(omega, src32, h->phys, h->fp32, count, h->stream), "qg_set_state: convert");
+  } else if (src32 == h->fp32) {
+    CK(cudaMemcpyAsync(h->phys, omega, count * h->esz, cudaMemcpyHostToDevice, h->stream), "qg_set_state: copy");
+    CK(cudaStreamSynchronize(h->stream), "qg_set_state: sync");
+  } else {
+    std::vector<double> v(count);
+    if (src32) for (size_t i = 0; i < count; ++i) v[i] = ((const float*)omega)[i];
+    else std::memcpy(v.data(), omega, count * 8);
+    int rc = upload_real(h, h->phys, v);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "qg_set_state: flag");
+  h->flag_pending = false;
+  *h->flag_host = 0;
+  RowDesc r{};
+  r.prog = RP_COPY;
+  r.nin = 1;
+  r.nout = 1;
+  r.in_phys = 1;
+  r.phys_in = h->phys;
+  r.out[0] = h->Y[0];
+  int rc = run_row(h, r, QG_K_OTHER, false);
+  if (rc) return rc;
+  ColDesc c = col_base(h);
+  c.op = CO_FORWARD;
+  c.nfwd = 1;
+  c.fin[0] = h->Y[0];
+  set_final(h, c);
+  return run_col(h, c, QG_K_OTHER, false);
+}
+
+int qg_get_state(qg_handle* h, void* omega, int32_t on_device, int32_t dtype) {
+  if (!h || !omega) return fail(QG_ERR_ARG, "qg_get_state: NULL argument");
+  if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_get_state: bad dtype");
+  int rc = state_to_phys(h);
+  if (rc) return rc;
+  const size_t count = (size_t)h->g.n * h->g.n;
+  const int dst32 = dtype == QG_FP32;
+  if (on_device) {
+    CK(launch_convert(h->phys, h->fp32, omega, dst32, count, h->stream), "qg_get_state: convert");
+    return QG_OK;
+  }
+  if (dst32 == h->fp32) {
+    CK(cudaMemcpyAsync(omega, h->phys, count * h->esz, cudaMemcpyDeviceToHost, h->stream), "qg_get_state: copy");
+    CK(cudaStreamSynchronize(h->stream), "qg_get_state: sync");
+    return QG_OK;
+  }
+  std::vector<unsigned char> tmp(count * h->esz);
+  CK(cudaMemcpyAsync(tmp.data(), h->phys, tmp.size(), cudaMemcpyDeviceToHost, h->stream), "qg_get_state: copy");
+  CK(cudaStreamSynchronize(h->stream), "qg_get_state: sync");
+  for (size_t i = 0; i < count; ++i) {
+    const double v = h->fp32 ? (double)((const float*)tmp.data())[i] : ((const double*)tmp.data())[i];
+    if (dst32) ((float*)omega)[i] = (float)v;
+    else ((double*)omega)[i] = v;
+  }
+  return QG_OK;
+}
+
+int qg_step(qg_handle* h, int32_t nsteps) {
+  if (!h) return fail(QG_ERR_ARG, "qg_step: NULL handle");
+  if (nsteps < 0) return fail(QG_ERR_ARG, "qg_step: nsteps < 0");
+  if (h->flag_pending && cudaEventQuery(h->flag_event) == cudaSuccess) h->flag_pending = false;
+  if (!h->flag_pending && *h->flag_host)
+    return fail(QG_ERR_NONFINITE, "qg_step: state became non-finite at an earlier step");
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = enqueue_step(h);
+    if (rc) return rc;
+  }
+  if (!h->flag_pending) {
+    CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "qg_step: flag");
+    CK(cudaEventRecord(h->flag_event, h->stream), "qg_step: event");
+    h->flag_pending = true;
+  }
+  return QG_OK;
+}
+
+int qg_sync(qg_handle* h) {
+  if (!h) return fail(QG_ERR_ARG, "qg_sync: NULL handle");
+  int f = 0;
+  CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "qg_sync: flag");
+  CK(cudaStreamSynchronize(h->stream), "qg_sync");
+  h->flag_pending = false;
+  f = *h->flag_host;
+  if (f) return fail(QG_ERR_NONFINITE, "qg_sync: state became non-finite");
+  return QG_OK;
+}
+
+int qg_diagnostics(qg_handle* h, qg_diag* out) {
+  if (!h || !out) return fail(QG_ERR_ARG, "qg_diagnostics: NULL argument");
+  int status = qg_sync(h);
+  if (status != QG_OK && status != QG_ERR_NONFINITE) return status;
+  const int nblk = 512;
+  double* sc = h->dev_scalars;
+  cudaError_t e = h->fp32 ? launch_spectral_sums<float>(h->g, h->w0, h->red, nblk, sc + 4, h->stream)
+                          : launch_spectral_sums<double>(h->g, h->w0, h->red, nblk, sc + 4, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "qg_diagnostics: sums");
+  int rc = state_to_phys(h);
+  if (rc) return rc;
+  e = h->fp32 ? launch_phys_maxabs<float>(h->g, h->phys, h->red, nblk, sc + 6, h->stream)
+              : launch_phys_maxabs<double>(h->g, h->phys, h->red, nblk, sc + 6, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "qg_diagnostics: max");
+  double host[16];
+  CK(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "qg_diagnostics: copy");
+  CK(cudaStreamSynchronize(h->stream), "qg_diagnostics: sync");
+  out->t = h->t;
+  out->step = h->step;
+  out->energy = host[4];
+  out->enstrophy = host[5];
+  out->coeff = h->dynamic ? host[2] : h->static_coeff;
+  out->max_abs_omega = host[6];
+  out->finite = (host[7] > 0.5 && status == QG_OK) ? 1 : 0;
+  out->reserved = 0;
+  if (!out->finite) return fail(QG_ERR_NONFINITE, "qg_diagnostics: state is not finite");
+  return QG_OK;
+}
+
+int qg_profile(qg_handle* h, int32_t enable) {
+  if (!h) return fail(QG_ERR_ARG, "qg_profile: NULL handle");
+  if (enable) {
+    CK(cudaStreamSynchronize(h->stream), "qg_profile: sync");
+    for (auto& r : h->recs) {
+      h->pool.push_back(r.a);
+      h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    for (int i = 0; i < QG_NUM_KCLASS; ++i) {
+      h->launches[i] = 0;
+      h->prof_ms[i] = 0.0;
+    }
+  }
+  h->prof = enable != 0;
+  return QG_OK;
+}
+
+int qg_kernel_times(qg_handle* h, int32_t* counts, double* ms, int32_t nclass) {
+  if (!h || nclass < 0 || nclass > QG_NUM_KCLASS) return fail(QG_ERR_ARG, "qg_kernel_times: bad argument");
+  CK(cudaStreamSynchronize(h->stream), "qg_kernel_times: sync");
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b), "qg_kernel_times: elapsed");
+    h->prof_ms[r.cls] += t;
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+  for (int i = 0; i < nclass; ++i) {
+    if (counts) counts[i] = h->launches[i];
+    if (ms) ms[i] = h->prof_ms[i];
+  }
+  return QG_OK;
+}
+
+}  // extern "C"

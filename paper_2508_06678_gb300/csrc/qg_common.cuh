@@ -1,0 +1,153 @@
+// Shared device types and layout descriptors of libqg.
+//
+// Layouts (all device-resident, owned by the handle):
+//   spectral  S[c * SP + r] : truncated half spectrum, column-major in k_x.
+//             c = m_x in [0, Kc), Kc = K + 1; r in [0, Ny), Ny = 2K + 1 with
+//             m_y = r for r <= K and m_y = r - Ny otherwise.  Only the modes
+//             the 2/3 rule keeps are stored (Sec. II-C); columns in
+//             [Kc, Kcp) are zero padding.
+//   mixed     I[y * IP + c]  : one field after the y-transform, rows y in
+//             [0, N), columns m_x in [0, Kcp).  The column pass writes it in
+//             W-wide tiles, the row pass reads whole rows.
+//   physical  f[y * N + x]   : real field.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qg {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename Cplx<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// (i s) * a for s = +1 / -1
+template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {
+  return s > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+// (i k) * a for real k
+template <typename C> __device__ __forceinline__ C cmul_ik(C a, decltype(C::x) k) { return mk<C>(-a.y * k, a.x * k); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+
+// Grid geometry shared by every kernel.
+struct Geom {
+  int n;      // grid size N
+  int K;      // 2/3-rule band limit floor((N-1)/3)
+  int Kc;     // K + 1 kept k_x columns
+  int Kcp;    // Kc rounded up to the column tile width
+  int Ny;     // 2K + 1 kept k_y rows
+  int SP;     // spectral column pitch (complex elements)
+  int IP;     // mixed-array row pitch (complex elements) = Kcp
+  double kscale;  // 2 pi / L
+};
+
+__host__ __device__ __forceinline__ int my_of_r(const Geom& g, int r) { return r <= g.K ? r : r - g.Ny; }
+// row of an N-point k_y sequence (FFT order) holding spectral index r
+__host__ __device__ __forceinline__ int row_of_r(const Geom& g, int r) { return r <= g.K ? r : g.n + r - g.Ny; }
+
+constexpr int kMaxIn = 12;   // max fields entering one row pass
+constexpr int kMaxOut = 6;   // max fields leaving one row pass
+constexpr int kMaxDer = 12;  // max derived fields leaving one column pass
+constexpr int kMaxFwd = 6;   // max fields entering one column pass
+
+// Codes of the spectral fields a column pass derives from a vorticity
+// spectrum w (all scaled by 1/N^2 so that the two inverse passes return
+// physical values).  The *_T codes apply the test filter first.
+enum DerCode : int {
+  D_U = 0,    // u_total = -d psi/dy + U
+  D_V = 1,    // v = d psi/dx
+  D_WX = 2,   // dw/dx
+  D_WY = 3,   // dw/dy
+  D_PXY = 4,  // d2 psi/dxdy
+  D_PD = 5,   // d2 psi/dx2 - d2 psi/dy2
+  D_W = 6,    // w itself
+  D_TEST = 8  // flag: test-filtered version of the code in the low bits
+};
+
+// Row-pass product programs.
+enum RowProg : int {
+  RP_NONE = 0,    // (u, v, wx, wy) -> J
+  RP_LEITH = 1,   // (u, v, wx, wy) -> J, g wx, g wy with g = |grad w|
+  RP_SMAG = 2,    // (u, v, wx, wy, pxy, pd) -> J, g wx, g wy with g = |S|
+  RP_DLEITH = 3,  // RP_LEITH at grid and test level
+  RP_DSMAG = 4,   // RP_SMAG at grid and test level
+  RP_SCALE = 5,   // f_i * factor(x, y) for each input (Brinkman, sponge)
+  RP_COPY = 6,    // identity (forward transform of a physical field, or inverse to physical)
+};
+
+// Column-pass operations.
+enum ColOp : int {
+  CO_DERIVE = 0,       // w <- stored state w0
+  CO_STAGE_STATIC = 1, // forward J[, P, Q]; L = -J - beta v + C D; RK combine
+  CO_DYN_REDUCE = 2,   // forward J, P, Q, J~, P~, Q~; store J, D; Germano partial sums
+  CO_DYN_COMBINE = 3,  // L = -J - beta v + C D with C from the partial sums; RK combine
+  CO_CURL = 4,         // forward u, v; w = i kx v - i ky u
+  CO_FORWARD = 5,      // forward one field; w = that field
+};
+
+struct RowDesc {
+  int prog;
+  int nin, nout;
+  int in_phys;   // inputs: 1 = physical rows from phys_in, 0 = mixed arrays in[]
+  int out_phys;  // outputs: 1 = physical rows to phys_out, 0 = mixed arrays out[]
+  unsigned dx_mask;  // bit f: multiply output f by i k_x after the forward transform
+  const void* in[kMaxIn];
+  void* out[kMaxOut];
+  const void* phys_in;
+  void* phys_out;
+  const void* factor;  // RP_SCALE: physical factor field
+  int check_finite;    // set *flag if a product is not finite
+  int* flag;
+};
+
+struct ColDesc {
+  int op;
+  int nfwd;
+  const void* fin[kMaxFwd];
+  int nder;
+  int der[kMaxDer];
+  void* dout[kMaxDer];
+  // spectral arrays
+  void* w0;        // state w^n (read; written when store_w0)
+  void* ws;        // RK stage state (read when use_ws; written when store_ws)
+  void* jh;        // dynamic closures: stored J_hat
+  void* dh;        // dynamic closures: stored D_hat
+  int use_ws;      // the stage input is ws (else w0)
+  int store_ws, store_w0;
+  int zero_mean;   // set the (0,0) mode to zero before storing / deriving
+  int viscous;     // multiply by exp(-(nu|k|^2 + mu) dt) after the combine
+  // RK combine w_new = a w0 + b (w_s + dt L)
+  double a, b, dt;
+  double beta, U;
+  double coeff;     // static closure coefficient C
+  int closure_pow;  // p of r^p in the Germano M
+  double test_ratio;
+  double rpow;      // r^p
+  // Germano partial sums: written by CO_DYN_REDUCE (2 doubles per block), read by CO_DYN_COMBINE
+  double* partials;
+  int npartials;
+  double* coeff_out;  // CO_DYN_COMBINE: block 0 writes C here
+  const void* visc_x;  // exp(-nu kx^2 dt), per m_x
+  const void* visc_y;  // exp(-nu ky^2 dt), per r
+  double visc_mu;      // exp(-mu dt)
+  int* flag;
+};
+
+}  // namespace qg

@@ -1,0 +1,195 @@
+"""Python names of the libqg C-ABI (include/qg.h).  Argument marshalling only.
+
+Host arrays are numpy float64/float32; device arrays are torch CUDA tensors
+(passed by data pointer, borrowed for the call).  Streams are torch streams
+or raw cudaStream_t integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._lib import (QG_ERR_NONFINITE, QG_FP32, QG_FP64, QG_OK, QGError, check, load, qg_closure, qg_diag, qg_grid,
+                   qg_params)
+
+__all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_step", "qg_sync", "qg_diagnostics", "qg_destroy",
+           "qg_sgs_apriori", "qg_last_error", "qg_version", "QGSolver"]
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def qg_last_error() -> str:
+    return load().qg_last_error().decode()
+
+
+def qg_version() -> str:
+    return load().qg_version().decode()
+
+
+def qg_create(grid: qg_grid, beta: float, U: float, mask, sponge, closure: qg_closure, params: qg_params,
+              stream=None) -> int:
+    """Create a solver; returns the opaque handle (int)."""
+    lib = load()
+    m = _dptr(mask)
+    s = _dptr(sponge)
+    n = grid.n
+    for name, arr in (("mask", m), ("sponge", s)):
+        if arr is not None and arr[0].size != n * n:
+            raise ValueError(f"{name} must hold n*n values")
+    out = C.c_void_p()
+    rc = lib.qg_create(C.byref(grid), float(beta), float(U), m[1] if m else None, s[1] if s else None,
+                       C.byref(closure), C.byref(params), _stream_ptr(stream), C.byref(out))
+    check(rc, "qg_create")
+    return out.value
+
+
+def _buffer(omega, n):
+    """(pointer, on_device, dtype, keepalive) of a host numpy array or a torch CUDA tensor."""
+    if hasattr(omega, "is_cuda") and omega.is_cuda:
+        import torch
+        if omega.numel() != n * n or not omega.is_contiguous():
+            raise ValueError("device field must be a contiguous tensor of n*n values")
+        if omega.dtype == torch.float64:
+            dt = QG_FP64
+        elif omega.dtype == torch.float32:
+            dt = QG_FP32
+        else:
+            raise TypeError("device field must be float32 or float64")
+        return omega.data_ptr(), 1, dt, omega
+    a = np.asarray(omega)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    a = np.ascontiguousarray(a)
+    if a.size != n * n:
+        raise ValueError("field must hold n*n values")
+    return a.ctypes.data, 0, (QG_FP32 if a.dtype == np.float32 else QG_FP64), a
+
+
+def qg_set_state(h: int, omega, n: int) -> None:
+    ptr, dev, dt, keep = _buffer(omega, n)
+    check(load().qg_set_state(h, ptr, dev, dt), "qg_set_state")
+    del keep
+
+
+def qg_get_state(h: int, n: int, out=None, dtype=np.float64):
+    """Physical vorticity: into ``out`` (numpy or torch CUDA tensor) or a new numpy array."""
+    if out is None:
+        out = np.empty((n, n), dtype=dtype)
+    ptr, dev, dt, keep = _buffer(out, n)
+    check(load().qg_get_state(h, ptr, dev, dt), "qg_get_state")
+    return out
+
+
+def qg_step(h: int, nsteps: int = 1) -> None:
+    check(load().qg_step(h, int(nsteps)), "qg_step")
+
+
+def qg_sync(h: int) -> None:
+    check(load().qg_sync(h), "qg_sync")
+
+
+def qg_diagnostics(h: int, raise_nonfinite: bool = True) -> dict:
+    d = qg_diag()
+    rc = load().qg_diagnostics(h, C.byref(d))
+    if rc != QG_OK and not (rc == QG_ERR_NONFINITE and not raise_nonfinite):
+        check(rc, "qg_diagnostics")
+    return {"t": d.t, "step": d.step, "energy": d.energy, "enstrophy": d.enstrophy, "coeff": d.coeff,
+            "max_abs_omega": d.max_abs_omega, "finite": bool(d.finite)}
+
+
+def qg_destroy(h: int) -> None:
+    if h:
+        load().qg_destroy(h)
+
+
+def qg_sgs_apriori(omega_fr, n_les: int, L: float, mask_fr, sponge_fr, closure: qg_closure, params: qg_params,
+                   U: float, beta: float, flags: int = 0):
+    """A priori SGS analysis; returns (pi_exact, pi_model, parts[3], pcc) as numpy arrays."""
+    w = _dptr(omega_fr)
+    n_fr = int(round(math.sqrt(w[0].size)))
+    m = _dptr(mask_fr)
+    s = _dptr(sponge_fr)
+    pe = np.zeros((n_les, n_les))
+    pm = np.zeros((n_les, n_les))
+    parts = np.zeros((3, n_les, n_les))
+    r = C.c_double(0.0)
+    P = C.POINTER(C.c_double)
+    rc = load().qg_sgs_apriori(w[1], n_fr, int(n_les), float(L), m[1] if m else None, s[1] if s else None,
+                               C.byref(closure), C.byref(params), float(U), float(beta), int(flags),
+                               pe.ctypes.data_as(P), pm.ctypes.data_as(P), parts.ctypes.data_as(P), C.byref(r))
+    check(rc, "qg_sgs_apriori")
+    return pe, pm, parts, r.value
+
+
+@dataclass
+class _Cfg:
+    n: int
+    L: float
+    precision: int
+
+
+class QGSolver:
+    """Owning wrapper of one libqg handle."""
+
+    def __init__(self, n: int, *, L: float = 2 * math.pi, precision: int = QG_FP64, beta: float = 0.0,
+                 U: float = 0.0, mask=None, sponge=None, kind: int = 0, c: float = 0.0, test_ratio: float = 2.0,
+                 dt: float = 2e-3, nu: float = 1.0 / 200.0, mu: float = 0.0, eta: float = 1e-3,
+                 sponge_rate: float = 50.0, stream=None):
+        self.cfg = _Cfg(n, L, precision)
+        self.h = 0
+        self.h = qg_create(qg_grid(n, precision, L), beta, U, mask, sponge, qg_closure(kind, 0, c, test_ratio),
+                           qg_params(dt, nu, mu, eta, sponge_rate), stream)
+
+    @classmethod
+    def from_workload(cls, wl, precision: int = QG_FP64, stream=None) -> "QGSolver":
+        return cls(wl.n, L=wl.L, precision=precision, beta=wl.beta, U=wl.U, mask=wl.mask(),
+                   sponge=wl.sponge_field(), kind=wl.closure, c=wl.c, test_ratio=wl.test_ratio, dt=wl.dt,
+                   nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, stream=stream)
+
+    def set_state(self, omega) -> None:
+        qg_set_state(self.h, omega, self.cfg.n)
+
+    def get_state(self, out=None, dtype=np.float64):
+        return qg_get_state(self.h, self.cfg.n, out, dtype)
+
+    def step(self, nsteps: int = 1) -> None:
+        qg_step(self.h, nsteps)
+
+    def sync(self) -> None:
+        qg_sync(self.h)
+
+    def diagnostics(self, raise_nonfinite: bool = True) -> dict:
+        return qg_diagnostics(self.h, raise_nonfinite)
+
+    def close(self) -> None:
+        if self.h:
+            qg_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

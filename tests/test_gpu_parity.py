@@ -1,0 +1,197 @@
+"""GPU (libqg, through the C-ABI) vs the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative L2 of the vorticity): FP64 1e-11 after 100 steps, FP32
+2e-4; single transforms and single steps far tighter.  Grid sizes span several
+column tiles with ragged tails (N = 18, 48, 54, 96 keep 6, 16, 18, 32 k_x
+columns against a tile width of 4 / 2), radix-3 sizes, and the full 2048^2
+production workload.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+
+pytestmark = pytest.mark.gpu
+
+qg = pytest.importorskip("paper_2508_06678_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_06678_gb300._lib import LIB_PATH
+    import os
+    if not os.path.exists(LIB_PATH):
+        from paper_2508_06678_gb300.build import build
+        build()
+    qg.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_pair(n, kind, *, geometry="island", beta=5.0, U=0.5, c=0.2, radius=0.8, sponge=True, seed=1,
+              k_peak=None, precision=qg.QG_FP64, dt=2e-3, nu=1.0 / 200, mu=0.0):
+    wl = S.Workload("t", n, geometry, beta=beta, U=U, closure=kind, c=c, radius=radius, seed=seed, sponge=sponge,
+                    dt=dt, nu=nu, mu=mu)
+    w0 = S.init_field(seed, n, k_peak=k_peak or max(4.0, n / 8))
+    mask = wl.mask() if geometry != "none" else None
+    sp = wl.sponge_field()
+    ref = O.QGOracle(n, wl.L, beta, U, mask, sp, O.Closure(kind, c=c), O.Params(dt=dt, nu=nu, mu=mu))
+    ref.set_state(w0)
+    gpu = qg.QGSolver(n, L=wl.L, precision=precision, beta=beta, U=U, mask=mask, sponge=sp, kind=kind, c=c,
+                      dt=dt, nu=nu, mu=mu)
+    gpu.set_state(w0)
+    return ref, gpu, w0
+
+
+@pytest.mark.parametrize("n", [16, 18, 24, 48, 54, 96, 128, 384, 512])
+@pytest.mark.parametrize("prec,tol", [(qg.QG_FP64, 1e-13), (qg.QG_FP32, 2e-6)])
+def test_projection_round_trip(n, prec, tol):
+    """set_state/get_state = forward then inverse 2-D transform with the 2/3 band (Sec. II-C)."""
+    ops = O.Ops(n)
+    rng = np.random.default_rng(n)
+    w = rng.standard_normal((n, n))
+    with qg.QGSolver(n, precision=prec) as s:
+        s.set_state(w)
+        got = s.get_state()
+    ref = O.to_physical(ops, O.project(ops, w))
+    assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+@pytest.mark.parametrize("n", [18, 48, 54])
+def test_one_step_parity_fp64(kind, n):
+    ref, gpu, _ = make_pair(n, kind, radius=0.9)
+    ref.step(1)
+    gpu.step(1)
+    assert rel(gpu.get_state(), ref.get_state()) < 1e-12
+    d = gpu.diagnostics()
+    if kind in (S.DSMAG, S.DLEITH):
+        assert d["coeff"] == pytest.approx(ref.last_coeff, rel=1e-9, abs=1e-300)
+    gpu.close()
+
+
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+def test_100_step_parity_fp64_island(kind):
+    ref, gpu, _ = make_pair(128, kind, radius=0.4, seed=0, k_peak=16.0)
+    ref.step(100)
+    gpu.step(100)
+    err = rel(gpu.get_state(), ref.get_state())
+    assert err < 1e-11, err
+    d = gpu.diagnostics()
+    r = ref.diagnostics()
+    assert d["energy"] == pytest.approx(r["energy"], rel=1e-11)
+    assert d["enstrophy"] == pytest.approx(r["enstrophy"], rel=1e-11)
+    assert d["max_abs_omega"] == pytest.approx(r["max_abs_omega"], rel=1e-10)
+    assert d["step"] == 100 and d["finite"]
+    gpu.close()
+
+
+@pytest.mark.parametrize("kind", [S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+def test_100_step_parity_fp32_cape(kind):
+    ref, gpu, _ = make_pair(96, kind, geometry="cape", beta=10.0, U=1.0, seed=2, k_peak=12.0,
+                            precision=qg.QG_FP32)
+    ref.step(100)
+    gpu.step(100)
+    err = rel(gpu.get_state(), ref.get_state())
+    assert err < 2e-4, err
+    gpu.close()
+
+
+@pytest.mark.parametrize("kind", [S.DSMAG, S.DLEITH])
+def test_dynamic_coefficient_is_active_and_matches(kind):
+    ref, gpu, _ = make_pair(48, kind, seed=1, k_peak=20.0)
+    for _ in range(3):
+        ref.step(1)
+        gpu.step(1)
+        d = gpu.diagnostics()
+        assert ref.last_coeff > 0
+        assert d["coeff"] == pytest.approx(ref.last_coeff, rel=1e-10)
+    gpu.close()
+
+
+def test_rossby_wave_matches_rk3_polynomial():
+    n, beta, U, dt, steps = 32, 5.0, 0.5, 2e-3, 50
+    x = np.arange(n) * (2 * math.pi / n)
+    w = np.cos(2 * x[None, :] + 3 * x[:, None] + 0.3)
+    with qg.QGSolver(n, beta=beta, U=U, dt=dt, nu=0.0) as s:
+        s.set_state(w)
+        s.step(steps)
+        got = s.get_state()
+    lam = 1j * 2 * (beta / 13.0 - U)
+    R = 1 + dt * lam + (dt * lam) ** 2 / 2 + (dt * lam) ** 3 / 6
+    ops = O.Ops(n)
+    expected = O.to_physical(ops, O.project(ops, w) * R ** steps)
+    assert rel(got, expected) < 1e-13
+
+
+def test_viscous_decay_exact():
+    n, nu, mu, dt, steps = 32, 0.05, 0.2, 1e-2, 40
+    x = np.arange(n) * (2 * math.pi / n)
+    w = np.sin(4 * x[None, :] - 3 * x[:, None])
+    with qg.QGSolver(n, dt=dt, nu=nu, mu=mu) as s:
+        s.set_state(w)
+        s.step(steps)
+        got = s.get_state()
+    assert np.max(np.abs(got - w * math.exp(-(nu * 25 + mu) * dt * steps))) < 1e-14
+
+
+def test_nonfinite_state_stops_and_reports():
+    n = 32
+    w = S.init_field(0, n)
+    w[3, 5] = np.nan
+    with qg.QGSolver(n, beta=1.0, U=0.3, kind=S.LEITH, c=0.2) as s:
+        s.set_state(w)
+        s.step(2)
+        with pytest.raises(qg.QGError) as ei:
+            s.sync()
+        assert ei.value.code == qg.QG_ERR_NONFINITE
+        with pytest.raises(qg.QGError):
+            s.step(1)
+        # a finite state resets the flag and stepping resumes
+        s.set_state(S.init_field(0, n))
+        s.step(1)
+        s.sync()
+
+
+@pytest.mark.parametrize("n", [15, 14, 20, 8, 8192])
+def test_bad_grid_sizes_rejected(n):
+    with pytest.raises(qg.QGError) as ei:
+        qg.QGSolver(n)
+    assert ei.value.code == qg.QG_ERR_ARG
+
+
+def test_device_state_io_with_torch():
+    import torch
+    n = 48
+    w = S.init_field(5, n)
+    with qg.QGSolver(n, precision=qg.QG_FP32, stream=torch.cuda.current_stream()) as s:
+        s.set_state(torch.tensor(w, dtype=torch.float32, device="cuda"))
+        out = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        s.get_state(out=out)
+        torch.cuda.synchronize()
+        ops = O.Ops(n)
+        assert rel(out.double().cpu().numpy(), O.to_physical(ops, O.project(ops, w))) < 2e-6
+
+
+def test_full_size_production_step_fp32():
+    """2048^2 dynamic Leith past an island, in the bench's launch configuration:
+    one step compared with the oracle over the whole field."""
+    wl = S.island2048_dleith()
+    n = wl.n
+    w0 = wl.omega0()
+    ref = O.QGOracle(n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure), O.Params())
+    ref.set_state(w0)
+    ref.step(1)
+    with qg.QGSolver.from_workload(wl, precision=qg.QG_FP32) as s:
+        s.set_state(w0)
+        s.step(1)
+        got = s.get_state()
+    assert rel(got, ref.get_state()) < 2e-5
