@@ -1,0 +1,158 @@
+// Register-resident FFT engine and the specialised row / column passes for
+// power-of-two grids (256 <= N <= 4096).
+//
+// Engine (E16): a length-N sequence is owned by TT = N/16 threads; thread t
+// holds the 16 elements at natural positions t + TT*m (m = 0..15).  A
+// Stockham DIT pass of radix R with span Ns splits the 16 elements into
+// 16/R butterflies (m = b + (16/R) r): butterfly j = t + TT b reads elements
+// j + (N/R) r, which are exactly the thread's own elements.  Its outputs go to
+// (j / Ns) Ns R + (j mod Ns) + Ns r; for every pass but the last that is a
+// shared-memory exchange (one barrier, buffers alternate), while the last pass
+// (Ns R = N) lands on t + TT m again.  Hence an inverse FFT, any pointwise
+// work and a forward FFT chain with no shared-memory traffic between them, and
+// every column-pass spectral operation happens in registers on the thread's
+// own k values.  Shared memory is padded by one element every 16 so the
+// exchanges are free of bank conflicts.
+//
+// Passes: radix 16 (as 4 x 4 with W16 twiddles) while possible, then one pass
+// of radix 8, 4 or 2.  Twiddles W_N^j come from a table computed on the host
+// from exactly reduced angles.
+#pragma once
+
+#include "fft.cuh"
+#include "qg_common.cuh"
+
+namespace qg {
+namespace fast {
+
+constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+template <typename C> __device__ __forceinline__ C cmulk(C a, decltype(C::x) c, decltype(C::x) s) {
+  return mk<C>(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <typename C> __device__ __forceinline__ void dft16(C* v, int s) {
+  using T = decltype(C::x);
+  const T c1 = T(0.92387953251128675613);  // cos(pi/8)
+  const T s1 = T(0.38268343236508977173);  // sin(pi/8)
+  const T h = T(0.70710678118654752440);
+  C a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C q[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+    dft4(q, s);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = q[k1];
+  }
+  // a[n2][k1] *= exp(s 2 pi i n2 k1 / 16)
+  const T ss = T(s);
+  a[1][1] = cmulk(a[1][1], c1, ss * s1);
+  a[1][2] = cmulk(a[1][2], h, ss * h);
+  a[1][3] = cmulk(a[1][3], s1, ss * c1);
+  a[2][1] = cmulk(a[2][1], h, ss * h);
+  a[2][2] = cmul_si(a[2][2], s);
+  a[2][3] = cmulk(a[2][3], -h, ss * h);
+  a[3][1] = cmulk(a[3][1], s1, ss * c1);
+  a[3][2] = cmulk(a[3][2], -h, ss * h);
+  a[3][3] = cmulk(a[3][3], -c1, -ss * s1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C q[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4(q, s);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = q[k2];
+  }
+}
+
+template <typename C, int R> __device__ __forceinline__ void dftR(C* v, int s) {
+  if constexpr (R == 16) dft16(v, s);
+  else if constexpr (R == 8) dft8(v, s);
+  else if constexpr (R == 4) dft4(v, s);
+  else dft2(v);
+}
+
+template <typename T, int N> struct E16 {
+  using C = cplx_t<T>;
+  static constexpr int TT = N / 16;
+  static constexpr int LOG2N = ilog2(N);
+  static constexpr int NP16 = LOG2N / 4;
+  static constexpr int RLAST = 1 << (LOG2N % 4);
+  static constexpr int BUF = N + N / 16;  // padded complex elements of one sequence
+  static constexpr int K = (N - 1) / 3;
+  static constexpr int Kc = K + 1;
+  static_assert((N & (N - 1)) == 0 && N >= 256 && N <= 4096, "E16 engine: N must be 2^p, 256..4096");
+
+  __device__ static __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+  // One Stockham pass; x in natural ownership on entry.  Non-last passes
+  // exchange through buf (stride `cs` complex between consecutive padded
+  // slots' owners is 1; `buf` already points at this sequence's slot area).
+  template <int R, int NS, bool LAST>
+  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* __restrict__ tw, int sign) {
+    constexpr int NB = 16 / R;
+    constexpr int TWS = N / (NS * R);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + TT * b;
+      const int k = j & (NS - 1);
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = x[b + NB * r];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = __ldg(&tw[r * k * TWS]);
+          if (sign > 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dftR<C, R>(v, sign);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b + NB * r] = v[r];
+      } else {
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad(base + NS * r)] = v[r];
+      }
+    }
+    if constexpr (!LAST) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = buf[pad(t + TT * m)];
+    }
+  }
+
+  // Full transform.  bufs[0], bufs[1] alternate per exchange (ph toggles);
+  // callers pass the same ph through every use of the two buffers.
+  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const C* __restrict__ tw, int sign) {
+    if constexpr (NP16 >= 1) {
+      constexpr bool last = (NP16 == 1 && RLAST == 1);
+      pass<16, 1, last>(x, t, ph ? b1 : b0, tw, sign);
+      if (!last) ph ^= 1;
+    }
+    if constexpr (NP16 >= 2) {
+      constexpr bool last = (NP16 == 2 && RLAST == 1);
+      pass<16, 16, last>(x, t, ph ? b1 : b0, tw, sign);
+      if (!last) ph ^= 1;
+    }
+    if constexpr (NP16 >= 3) {
+      constexpr bool last = (NP16 == 3 && RLAST == 1);
+      pass<16, 256, last>(x, t, ph ? b1 : b0, tw, sign);
+      if (!last) ph ^= 1;
+    }
+    if constexpr (RLAST > 1) {
+      constexpr int NS = N / RLAST;
+      pass<RLAST, NS, true>(x, t, ph ? b1 : b0, tw, sign);
+    }
+  }
+};
+
+}  // namespace fast
+
+template <typename T, int N>
+cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st);
+template <typename T, int N>
+cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cudaStream_t st);
+
+}  // namespace qg

@@ -1,0 +1,578 @@
+// Specialised row / column passes for power-of-two N on the E16 engine.
+// Same arithmetic and data layouts as row.cu / column.cu (see there for the
+// equations); only the FFT organisation differs.  Included by fast_<N>.cu,
+// one translation unit per grid size.
+#pragma once
+
+#include "fast.cuh"
+#include "qg_kernels.h"
+
+namespace qg {
+namespace fast {
+
+template <int N> struct RowCfg {
+  static constexpr int TT = N / 16;
+  static constexpr int ROWS = TT >= 128 ? 1 : 128 / TT;
+  static constexpr int THREADS = TT * ROWS;
+};
+
+template <int N> struct ColCfg {
+  static constexpr int W = 2;  // k_x columns per CTA
+  static constexpr int TT = N / 16;
+  static constexpr int THREADS = W * TT;
+  static constexpr int CP = N + N / 16 + 8;  // column stride in shared memory (complex); = 8 mod 16
+};
+
+template <typename T>
+__device__ __forceinline__ void leith_p(T u, T v, T wx, T wy, T& J, T& P, T& Q) {
+  J = u * wx + v * wy;
+  const T g = sqrt(wx * wx + wy * wy);
+  P = g * wx;
+  Q = g * wy;
+}
+
+template <typename T>
+__device__ __forceinline__ void smag_p(T u, T v, T wx, T wy, T pxy, T pd, T& J, T& P, T& Q) {
+  J = u * wx + v * wy;
+  const T g = sqrt(T(4) * pxy * pxy + pd * pd);
+  P = g * wx;
+  Q = g * wy;
+}
+
+// ---------------------------------------------------------------------------
+// Row pass
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct RowCtx {
+  using E = E16<T, N>;
+  using C = cplx_t<T>;
+  static constexpr int TT = E::TT;
+  int t, y;
+  C* b0;
+  C* b1;
+  int ph;
+  const C* tw;
+  const Geom* g;
+  int bad;
+
+  // inverse x-transform of the pair (A + i B) of half-spectrum rows; B may be null
+  __device__ __forceinline__ void inv_pair(C* x, const void* Av, const void* Bv) {
+    const C* A = reinterpret_cast<const C*>(Av) + (size_t)y * g->IP;
+    const C* B = Bv ? reinterpret_cast<const C*>(Bv) + (size_t)y * g->IP : nullptr;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = t + TT * m;
+      C z = mk<C>(T(0), T(0));
+      if (k <= E::K) {
+        C a = A[k];
+        C b = B ? B[k] : mk<C>(T(0), T(0));
+        if (k == 0) {
+          a.y = T(0);
+          b.y = T(0);
+        }
+        z = mk<C>(a.x - b.y, a.y + b.x);
+      } else if (k >= N - E::K) {
+        const C a = A[N - k];
+        const C b = B ? B[N - k] : mk<C>(T(0), T(0));
+        z = mk<C>(a.x + b.y, b.x - a.y);
+      }
+      x[m] = z;
+    }
+    E::run(x, t, b0, b1, ph, tw, +1);
+  }
+
+  // forward x-transform of (re, im) = two real rows, split, optional i k_x, store kept columns
+  __device__ __forceinline__ void fwd_store(C* x, void* Av, void* Bv, bool dxa, bool dxb) {
+    E::run(x, t, b0, b1, ph, tw, -1);
+    C* ub = ph ? b1 : b0;
+    ph ^= 1;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) ub[E::pad(t + TT * m)] = x[m];
+    __syncthreads();
+    C* A = reinterpret_cast<C*>(Av) + (size_t)y * g->IP;
+    C* B = Bv ? reinterpret_cast<C*>(Bv) + (size_t)y * g->IP : nullptr;
+    const T ks = T(g->kscale);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = t + TT * m;
+      if (k < g->Kcp) {
+        C a = mk<C>(T(0), T(0)), b = mk<C>(T(0), T(0));
+        if (k < E::Kc) {
+          const C z = x[m];
+          const C zm = ub[E::pad((N - k) & (N - 1))];
+          a = mk<C>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
+          b = mk<C>(T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x));
+          const T kx = ks * T(k);
+          if (dxa) a = cmul_ik(a, kx);
+          if (dxb) b = cmul_ik(b, kx);
+        }
+        A[k] = a;
+        if (B) B[k] = b;
+      }
+    }
+  }
+
+  __device__ __forceinline__ void check(const T* v) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) bad |= !isfinite(v[m]);
+  }
+};
+
+// One level of the stage products: inverse-transform (u, v), (w_x, w_y)
+// [and (psi_xy, psi_xx - psi_yy)] and form J = u w_x + v w_y, P = g w_x,
+// Q = g w_y with g = |grad w| (Leith) or |S| (Smagorinsky); NONE forms J only.
+template <typename T, int N, bool SMAG, bool NONE>
+__device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, const void* const* in, T* J, T* P,
+                                               T* Q) {
+  using C = cplx_t<T>;
+  cx.inv_pair(x, in[0], in[1]);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    J[m] = x[m].x;  // u_total
+    P[m] = x[m].y;  // v
+  }
+  cx.inv_pair(x, in[2], in[3]);  // (w_x, w_y)
+  if constexpr (SMAG) {
+    C s[16];
+    cx.inv_pair(s, in[4], in[5]);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      T j, p, q;
+      smag_p<T>(J[m], P[m], x[m].x, x[m].y, s[m].x, s[m].y, j, p, q);
+      J[m] = j;
+      P[m] = p;
+      Q[m] = q;
+    }
+  } else if constexpr (NONE) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) J[m] = J[m] * x[m].x + P[m] * x[m].y;
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      T j, p, q;
+      leith_p<T>(J[m], P[m], x[m].x, x[m].y, j, p, q);
+      J[m] = j;
+      P[m] = p;
+      Q[m] = q;
+    }
+  }
+  cx.check(J);
+  if constexpr (!NONE) {
+    cx.check(P);
+    cx.check(Q);
+  }
+}
+
+template <typename T, int N, int PROG>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) row_fast_kernel(Geom g, RowDesc d,
+                                                                       const cplx_t<T>* __restrict__ tw) {
+  using E = E16<T, N>;
+  using C = cplx_t<T>;
+  constexpr int TT = E::TT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int lr = threadIdx.x / TT;
+  RowCtx<T, N> cx;
+  cx.t = threadIdx.x % TT;
+  cx.y = blockIdx.x * RowCfg<N>::ROWS + lr;
+  cx.b0 = sm + (size_t)(2 * lr) * E::BUF;
+  cx.b1 = cx.b0 + E::BUF;
+  cx.ph = 0;
+  cx.tw = tw;
+  cx.g = &g;
+  cx.bad = 0;
+  if (d.flag) {
+    if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
+  }
+  const int t = cx.t;
+  const size_t yN = (size_t)cx.y * N;
+  C x[16];
+
+  if constexpr (PROG == RP_NONE || PROG == RP_LEITH || PROG == RP_SMAG || PROG == RP_DLEITH || PROG == RP_DSMAG) {
+    constexpr bool smag = PROG == RP_SMAG || PROG == RP_DSMAG;
+    constexpr bool dyn = PROG == RP_DLEITH || PROG == RP_DSMAG;
+    constexpr bool none = PROG == RP_NONE;
+    constexpr int per = smag ? 6 : 4;  // inputs per level
+    T J[16], P[16], Q[16];
+    level_products<T, N, smag, none>(cx, x, d.in + 0, J, P, Q);
+    if constexpr (none) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], T(0));
+      cx.fwd_store(x, d.out[0], nullptr, false, false);
+    } else {
+      // outputs: 0 J, 1 P (times i k_x), 2 Q [, 3 J~, 4 P~ (times i k_x), 5 Q~]
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], P[m]);
+      cx.fwd_store(x, d.out[0], d.out[1], false, true);
+      if constexpr (!dyn) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m] = mk<C>(Q[m], T(0));
+        cx.fwd_store(x, d.out[2], nullptr, false, false);
+      } else {
+        T Qk[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) Qk[m] = Q[m];
+        level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m] = mk<C>(Qk[m], Q[m]);
+        cx.fwd_store(x, d.out[2], d.out[5], false, false);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], P[m]);
+        cx.fwd_store(x, d.out[3], d.out[4], false, true);
+      }
+    }
+  } else if constexpr (PROG == RP_SCALE) {
+    // Brinkman (2 fields) or sponge (1 field): multiply by the exact factor field
+    const T* fac = reinterpret_cast<const T*>(d.factor) + yN;
+    cx.inv_pair(x, d.in[0], d.nin > 1 ? d.in[1] : nullptr);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const T f = fac[t + TT * m];
+      x[m] = mk<C>(x[m].x * f, x[m].y * f);
+      cx.bad |= !isfinite(x[m].x) | !isfinite(x[m].y);
+    }
+    cx.fwd_store(x, d.out[0], d.nout > 1 ? d.out[1] : nullptr, false, false);
+  } else {  // RP_COPY: physical row in or out
+    if (d.in_phys) {
+      const T* src = reinterpret_cast<const T*>(d.phys_in) + yN;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = mk<C>(src[t + TT * m], T(0));
+      cx.fwd_store(x, d.out[0], nullptr, false, false);
+    } else {
+      cx.inv_pair(x, d.in[0], nullptr);
+      T* dst = reinterpret_cast<T*>(d.phys_out) + yN;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) dst[t + TT * m] = x[m].x;
+    }
+  }
+  if (d.check_finite && d.flag) {
+    if (__syncthreads_or(cx.bad) && threadIdx.x == 0) atomicOr(d.flag, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass
+// ---------------------------------------------------------------------------
+template <typename T> struct FInvK2;
+template <> struct FInvK2<double> {
+  __device__ static double get(double ks2, int m2) { return m2 == 0 ? 0.0 : 1.0 / (ks2 * double(m2)); }
+};
+template <> struct FInvK2<float> {
+  __device__ static float get(double ks2, int m2) {
+    if (m2 == 0) return 0.f;
+    if (m2 <= 16) return float(1.0 / (ks2 * double(m2)));
+    return 1.f / (float(ks2) * float(m2));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ cplx_t<T> fderive(int code, cplx_t<T> w, int mx, int my, double kscale, double ks2,
+                                             double test_lim, double n2, T scale, T U) {
+  using C = cplx_t<T>;
+  const int m2 = mx * mx + my * my;
+  if ((code & D_TEST) && double(m2) * test_lim > n2) w = mk<C>(T(0), T(0));
+  const T kx = T(kscale) * T(mx);
+  const T ky = T(kscale) * T(my);
+  const T ik2 = FInvK2<T>::get(ks2, m2);
+  const C psi = mk<C>(-w.x * ik2, -w.y * ik2);
+  C v;
+  switch (code & 7) {
+    case D_U: v = cmul_ik(psi, -ky); break;
+    case D_V: v = cmul_ik(psi, kx); break;
+    case D_WX: v = cmul_ik(w, kx); break;
+    case D_WY: v = cmul_ik(w, ky); break;
+    case D_PXY: v = cscale(psi, -(kx * ky)); break;
+    case D_PD: v = cscale(psi, -(kx * kx - ky * ky)); break;
+    default: v = w; break;
+  }
+  v = cscale(v, scale);
+  if ((code & 7) == D_U && m2 == 0) v = mk<C>(U, T(0));
+  return v;
+}
+
+template <typename T, int N, int OP>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, ColDesc d,
+                                                                       const cplx_t<T>* __restrict__ tw) {
+  using E = E16<T, N>;
+  using C = cplx_t<T>;
+  constexpr int W = ColCfg<N>::W;
+  constexpr int TT = E::TT;
+  constexpr int CP = ColCfg<N>::CP;
+  constexpr int K = E::K;
+  constexpr int Ny = 2 * K + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[2][32];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int mx = blockIdx.x * W + c;
+  const bool col_ok = mx < E::Kc;
+  C* b0 = sm + c * CP;
+  C* b1 = sm + (W + c) * CP;
+  int ph = 0;
+  if (d.flag) {
+    if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
+  }
+  const double ks2 = g.kscale * g.kscale;
+  const double test_lim = 4.0 * d.test_ratio * d.test_ratio;
+  const double n2 = double(N) * double(N);
+  const T kxv = T(g.kscale) * T(mx);
+  C* w0 = reinterpret_cast<C*>(d.w0);
+  C* ws = reinterpret_cast<C*>(d.ws);
+  C* jh = reinterpret_cast<C*>(d.jh);
+  C* dh = reinterpret_cast<C*>(d.dh);
+  const size_t colbase = (size_t)mx * g.SP;
+
+  C x[16], A[16], B[16];
+  double hm = 0.0, mm = 0.0;
+
+  // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
+  if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
+#pragma unroll 1
+    for (int f = 0; f < d.nfwd; ++f) {
+      const C* src = reinterpret_cast<const C*>(d.fin[f]) + mx;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = src[(size_t)(t + TT * m) * g.IP];
+      E::run(x, t, b0, b1, ph, tw, -1);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k = t + TT * m;
+        const int my = k <= K ? k : k - N;
+        const T ky = T(g.kscale) * T(my);
+        C X = col_ok ? x[m] : mk<C>(T(0), T(0));
+        if constexpr (OP == CO_STAGE_STATIC) {
+          if (f == 0) A[m] = mk<C>(-X.x, -X.y);
+          else if (f == 1) B[m] = X;
+          else B[m] = cadd(B[m], cmul_ik(X, ky));
+        } else if constexpr (OP == CO_DYN_REDUCE) {
+          const bool kept = k <= K || k >= N - K;
+          const int r = k <= K ? k : k - N + Ny;
+          const bool in_test = double(mx * mx + my * my) * test_lim <= n2;
+          if (f == 0) {
+            A[m] = X;
+            if (kept) jh[colbase + r] = X;
+          } else if (f == 1) {
+            B[m] = X;
+          } else if (f == 2) {
+            const C D = cadd(B[m], cmul_ik(X, ky));
+            if (kept) dh[colbase + r] = D;
+            B[m] = in_test ? mk<C>(-D.x, -D.y) : mk<C>(T(0), T(0));
+          } else if (f == 3) {
+            A[m] = in_test ? csub(X, A[m]) : X;
+          } else if (f == 4) {
+            B[m] = cadd(B[m], cscale(X, T(d.rpow)));
+          } else {
+            const C M = cadd(B[m], cscale(cmul_ik(X, ky), T(d.rpow)));
+            const C H = A[m];
+            if (kept && col_ok) {
+              const double wgt = mx == 0 ? 1.0 : 2.0;
+              hm += wgt * (double(H.x) * double(M.x) + double(H.y) * double(M.y));
+              mm += wgt * (double(M.x) * double(M.x) + double(M.y) * double(M.y));
+            }
+          }
+        } else if constexpr (OP == CO_CURL) {
+          if (f == 0) A[m] = X;
+          else A[m] = csub(cmul_ik(X, kxv), cmul_ik(A[m], ky));
+        } else {  // CO_FORWARD
+          A[m] = X;
+        }
+      }
+    }
+  }
+
+  if constexpr (OP == CO_DYN_REDUCE) {
+    for (int o = 16; o > 0; o >>= 1) {
+      hm += __shfl_down_sync(0xffffffffu, hm, o);
+      mm += __shfl_down_sync(0xffffffffu, mm, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][wid] = hm;
+      red[1][wid] = mm;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      constexpr int nw = (ColCfg<N>::THREADS + 31) / 32;
+      hm = lane < nw ? red[0][lane] : 0.0;
+      mm = lane < nw ? red[1][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        hm += __shfl_down_sync(0xffffffffu, hm, o);
+        mm += __shfl_down_sync(0xffffffffu, mm, o);
+      }
+      if (lane == 0) {
+        d.partials[2 * blockIdx.x] = hm;
+        d.partials[2 * blockIdx.x + 1] = mm;
+      }
+    }
+    return;
+  } else {
+    T coeff = T(d.coeff);
+    if constexpr (OP == CO_DYN_COMBINE) {
+      if (threadIdx.x < 32) {
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < d.npartials; i += 32) {
+          a += d.partials[2 * i];
+          b += d.partials[2 * i + 1];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_down_sync(0xffffffffu, a, o);
+          b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (threadIdx.x == 0) {
+          const double Cc = b > 0.0 ? fmax(0.0, a / b) : 0.0;
+          red[0][0] = Cc;
+          if (blockIdx.x == 0 && d.coeff_out) *d.coeff_out = Cc;
+        }
+      }
+      __syncthreads();
+      coeff = T(red[0][0]);
+    }
+
+    // ---- new state per owned mode (registers A)
+    const T dt = T(d.dt), a_rk = T(d.a), b_rk = T(d.b), beta = T(d.beta);
+    const T* vx = reinterpret_cast<const T*>(d.visc_x);
+    const T* vy = reinterpret_cast<const T*>(d.visc_y);
+    const T vmu = T(d.visc_mu);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = t + TT * m;
+      const bool kept = (k <= K || k >= N - K) && col_ok;
+      const int r = k <= K ? k : k - N + Ny;
+      const int my = k <= K ? k : k - N;
+      C wn = mk<C>(T(0), T(0));
+      if (kept) {
+        const size_t gi = colbase + r;
+        if constexpr (OP == CO_DERIVE) {
+          wn = w0[gi];
+        } else if constexpr (OP == CO_STAGE_STATIC || OP == CO_DYN_COMBINE) {
+          const C wz = w0[gi];
+          const C wst = d.use_ws ? ws[gi] : wz;
+          const T ik2 = FInvK2<T>::get(ks2, mx * mx + my * my);
+          const C psi = mk<C>(-wst.x * ik2, -wst.y * ik2);
+          const C bv = cscale(cmul_ik(psi, kxv), beta);
+          C L;
+          if constexpr (OP == CO_STAGE_STATIC) {
+            L = csub(A[m], bv);
+            if (d.nfwd > 1) L = cadd(L, cscale(B[m], coeff));
+          } else {
+            const C J = jh[gi];
+            L = csub(mk<C>(-J.x, -J.y), bv);
+            L = cadd(L, cscale(dh[gi], coeff));
+          }
+          const C inner = cadd(wst, cscale(L, dt));
+          wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
+        } else {
+          wn = A[m];
+        }
+        if (d.viscous) wn = cscale(wn, vx[mx] * vy[r] * vmu);
+        if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
+        if (d.store_ws) ws[gi] = wn;
+        if (d.store_w0) w0[gi] = wn;
+      }
+      A[m] = wn;
+    }
+
+    // ---- derived fields, inverse y-transforms, mixed arrays out
+    const T scale = T(1.0 / n2);
+    const T U = T(d.U);
+#pragma unroll 1
+    for (int q = 0; q < d.nder; ++q) {
+      const int code = d.der[q];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k = t + TT * m;
+        const bool kept = (k <= K || k >= N - K) && col_ok;
+        const int my = k <= K ? k : k - N;
+        x[m] = kept ? fderive<T>(code, A[m], mx, my, g.kscale, ks2, test_lim, n2, scale, U) : mk<C>(T(0), T(0));
+      }
+      E::run(x, t, b0, b1, ph, tw, +1);
+      C* dst = reinterpret_cast<C*>(d.dout[q]) + mx;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) dst[(size_t)(t + TT * m) * g.IP] = x[m];
+    }
+  }
+}
+
+}  // namespace fast
+
+template <typename T, int N>
+cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st) {
+  using E = fast::E16<T, N>;
+  using Cfg = fast::RowCfg<N>;
+  const size_t smem = (size_t)2 * Cfg::ROWS * E::BUF * sizeof(cplx_t<T>);
+  const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);
+  const int grid = N / Cfg::ROWS;
+  cudaError_t e = cudaSuccess;
+#define QG_ROW_CASE(P)                                                                                   \
+  case P: {                                                                                              \
+    auto k = fast::row_fast_kernel<T, N, P>;                                                            \
+    static unsigned long long attr_done = 0ull;                                                         \
+    int dev_ = 0;                                                                                        \
+    cudaGetDevice(&dev_);                                                                                \
+    if (dev_ >= 64 || !(attr_done >> dev_ & 1ull)) {                                                     \
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
+      if (e != cudaSuccess) return e;                                                                    \
+      if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
+    }                                                                                                    \
+    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp);                                                     \
+    break;                                                                                               \
+  }
+  switch (d.prog) {
+    QG_ROW_CASE(RP_NONE)
+    QG_ROW_CASE(RP_LEITH)
+    QG_ROW_CASE(RP_SMAG)
+    QG_ROW_CASE(RP_DLEITH)
+    QG_ROW_CASE(RP_DSMAG)
+    QG_ROW_CASE(RP_SCALE)
+    QG_ROW_CASE(RP_COPY)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef QG_ROW_CASE
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cudaStream_t st) {
+  using E = fast::E16<T, N>;
+  using Cfg = fast::ColCfg<N>;
+  const size_t smem = (size_t)2 * Cfg::W * Cfg::CP * sizeof(cplx_t<T>);
+  const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);
+  const int grid = g.Kcp / Cfg::W;
+  cudaError_t e = cudaSuccess;
+#define QG_COL_CASE(P)                                                                                   \
+  case P: {                                                                                              \
+    auto k = fast::col_fast_kernel<T, N, P>;                                                            \
+    static unsigned long long attr_done = 0ull;                                                         \
+    int dev_ = 0;                                                                                        \
+    cudaGetDevice(&dev_);                                                                                \
+    if (dev_ >= 64 || !(attr_done >> dev_ & 1ull)) {                                                     \
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
+      if (e != cudaSuccess) return e;                                                                    \
+      if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
+    }                                                                                                    \
+    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp);                                                     \
+    break;                                                                                               \
+  }
+  switch (d.op) {
+    QG_COL_CASE(CO_DERIVE)
+    QG_COL_CASE(CO_STAGE_STATIC)
+    QG_COL_CASE(CO_DYN_REDUCE)
+    QG_COL_CASE(CO_DYN_COMBINE)
+    QG_COL_CASE(CO_CURL)
+    QG_COL_CASE(CO_FORWARD)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef QG_COL_CASE
+  (void)E::BUF;
+  return cudaGetLastError();
+}
+
+#define QG_INSTANTIATE_FAST(N)                                                                          \
+  template cudaError_t launch_row_fast<float, N>(const Geom&, const RowDesc&, const void*, cudaStream_t);  \
+  template cudaError_t launch_row_fast<double, N>(const Geom&, const RowDesc&, const void*, cudaStream_t); \
+  template cudaError_t launch_col_fast<float, N>(const Geom&, const ColDesc&, const void*, cudaStream_t);  \
+  template cudaError_t launch_col_fast<double, N>(const Geom&, const ColDesc&, const void*, cudaStream_t);
+
+}  // namespace qg

@@ -18,11 +18,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/qg.h"
+#include "fast.cuh"
 #include "qg_kernels.h"
 
 using namespace qg;
@@ -123,6 +125,7 @@ struct qg_handle {
   int W = 4, col_threads = 256, row_threads = 256;
   size_t col_smem = 0, row_smem = 0;
   int ncolblk = 0;
+  bool fast = false;  // power-of-two grid served by the register-resident FFT kernels
   bool dynamic = false;
   double static_coeff = 0.0;
   // stage program
@@ -230,11 +233,39 @@ struct Bracket {
   }
 };
 
+template <typename T>
+cudaError_t row_fast_dispatch(qg_handle* h, const RowDesc& d) {
+  switch (h->g.n) {
+    case 256: return launch_row_fast<T, 256>(h->g, d, h->tw, h->stream);
+    case 512: return launch_row_fast<T, 512>(h->g, d, h->tw, h->stream);
+    case 1024: return launch_row_fast<T, 1024>(h->g, d, h->tw, h->stream);
+    case 2048: return launch_row_fast<T, 2048>(h->g, d, h->tw, h->stream);
+    case 4096: return launch_row_fast<T, 4096>(h->g, d, h->tw, h->stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
+  switch (h->g.n) {
+    case 256: return launch_col_fast<T, 256>(h->g, d, h->tw, h->stream);
+    case 512: return launch_col_fast<T, 512>(h->g, d, h->tw, h->stream);
+    case 1024: return launch_col_fast<T, 1024>(h->g, d, h->tw, h->stream);
+    case 2048: return launch_col_fast<T, 2048>(h->g, d, h->tw, h->stream);
+    case 4096: return launch_col_fast<T, 4096>(h->g, d, h->tw, h->stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
   Bracket br(h, cls);
-  cudaError_t e = h->fp32 ? launch_row<float>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream)
-                          : launch_row<double>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream);
+  cudaError_t e;
+  if (h->fast)
+    e = h->fp32 ? row_fast_dispatch<float>(h, d) : row_fast_dispatch<double>(h, d);
+  else
+    e = h->fp32 ? launch_row<float>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream)
+                : launch_row<double>(h->g, h->plan, d, h->tw, h->row_threads, h->row_smem, h->stream);
   br.done();
   if (e != cudaSuccess) return cuda_fail(e, "row pass launch");
   return QG_OK;
@@ -243,8 +274,12 @@ int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
 int run_col(qg_handle* h, ColDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
   Bracket br(h, cls);
-  cudaError_t e = h->fp32 ? launch_col<float>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream)
-                          : launch_col<double>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream);
+  cudaError_t e;
+  if (h->fast)
+    e = h->fp32 ? col_fast_dispatch<float>(h, d) : col_fast_dispatch<double>(h, d);
+  else
+    e = h->fp32 ? launch_col<float>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream)
+                : launch_col<double>(h->g, h->plan, d, h->tw, h->W, h->col_threads, h->col_smem, h->stream);
   br.done();
   if (e != cudaSuccess) return cuda_fail(e, "column pass launch");
   return QG_OK;
@@ -517,6 +552,15 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     delete h;
     return fail(QG_ERR_UNSUPPORTED, "qg_create: row pass needs %zu B of shared memory (n=%d, closure %d)",
                 h->row_smem, n, closure->kind);
+  }
+  // power-of-two grids use the register-resident kernels (two k_x columns per CTA)
+  {
+    const bool pow2 = (n & (n - 1)) == 0 && n >= 256 && n <= 4096;
+    const size_t fast_col_smem = (size_t)2 * 2 * (n + n / 16 + 8) * csz;
+    const size_t fast_row_smem = (size_t)2 * (n >= 2048 ? 1 : 2048 / n) * (n + n / 16) * csz;
+    h->fast = pow2 && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
+    if (getenv("QG_FORCE_GENERIC")) h->fast = false;
+    if (h->fast) h->W = 2;
   }
   g.Kcp = (g.Kc + h->W - 1) / h->W * h->W;
   g.IP = g.Kcp;

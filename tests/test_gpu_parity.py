@@ -51,7 +51,7 @@ def make_pair(n, kind, *, geometry="island", beta=5.0, U=0.5, c=0.2, radius=0.8,
     return ref, gpu, w0
 
 
-@pytest.mark.parametrize("n", [16, 18, 24, 48, 54, 96, 128, 384, 512])
+@pytest.mark.parametrize("n", [16, 18, 24, 48, 54, 96, 128, 256, 384, 512, 1024, 2048, 4096])
 @pytest.mark.parametrize("prec,tol", [(qg.QG_FP64, 1e-13), (qg.QG_FP32, 2e-6)])
 def test_projection_round_trip(n, prec, tol):
     """set_state/get_state = forward then inverse 2-D transform with the 2/3 band (Sec. II-C)."""
@@ -79,8 +79,10 @@ def test_one_step_parity_fp64(kind, n):
 
 
 @pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
-def test_100_step_parity_fp64_island(kind):
-    ref, gpu, _ = make_pair(128, kind, radius=0.4, seed=0, k_peak=16.0)
+@pytest.mark.parametrize("n", [128, 256])
+def test_100_step_parity_fp64_island(kind, n):
+    """128^2 runs the generic kernels, 256^2 the register-resident power-of-two kernels."""
+    ref, gpu, _ = make_pair(n, kind, radius=0.4, seed=0, k_peak=16.0)
     ref.step(100)
     gpu.step(100)
     err = rel(gpu.get_state(), ref.get_state())
@@ -94,9 +96,10 @@ def test_100_step_parity_fp64_island(kind):
     gpu.close()
 
 
-@pytest.mark.parametrize("kind", [S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
-def test_100_step_parity_fp32_cape(kind):
-    ref, gpu, _ = make_pair(96, kind, geometry="cape", beta=10.0, U=1.0, seed=2, k_peak=12.0,
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+@pytest.mark.parametrize("n", [96, 256])
+def test_100_step_parity_fp32_cape(kind, n):
+    ref, gpu, _ = make_pair(n, kind, geometry="cape", beta=10.0, U=1.0, seed=2, k_peak=12.0,
                             precision=qg.QG_FP32)
     ref.step(100)
     gpu.step(100)
@@ -195,3 +198,23 @@ def test_full_size_production_step_fp32():
         s.step(1)
         got = s.get_state()
     assert rel(got, ref.get_state()) < 2e-5
+
+
+@pytest.mark.parametrize("kind", [S.SMAG, S.DLEITH])
+@pytest.mark.parametrize("prec,tol", [(qg.QG_FP64, 1e-12), (qg.QG_FP32, 2e-5)])
+def test_fast_and_generic_kernels_agree(kind, prec, tol, monkeypatch):
+    """The power-of-two kernels and the generic mixed-radix kernels compute the same step."""
+    n = 512
+    wl = S.Workload("t", n, "island", beta=5.0, U=0.5, closure=kind, c=0.2, radius=0.6, seed=7)
+    w0 = S.init_field(7, n, k_peak=40.0)
+    out = []
+    for generic in (False, True):
+        if generic:
+            monkeypatch.setenv("QG_FORCE_GENERIC", "1")
+        else:
+            monkeypatch.delenv("QG_FORCE_GENERIC", raising=False)
+        with qg.QGSolver.from_workload(wl, precision=prec) as s:
+            s.set_state(w0)
+            s.step(10)
+            out.append(s.get_state())
+    assert rel(out[0], out[1]) < tol
