@@ -71,11 +71,15 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str = LIB_PATH) -> C.CDLL:
-    """Load libqg and declare every entry point; raises if the build is missing."""
+def load(path: str | None = None) -> C.CDLL:
+    """Load libqg and declare every entry point; raises if the build is missing.
+
+    The environment variable QG_LIB selects another build of the library.
+    """
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("QG_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libqg is not built ({path} missing): run __graft_entry__.build() first")
     lib = C.CDLL(path)

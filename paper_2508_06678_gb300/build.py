@@ -30,11 +30,11 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     srcs = sources()
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
@@ -48,13 +48,14 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         for msg in ex.map(compile_one, zip(srcs, objs)):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    tmp = LIB + ".tmp"
+    lib = os.path.join(out_dir, "libqg.so")
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -35,12 +35,10 @@ template <> struct InvK2<float> {
 
 template <typename T>
 __device__ __forceinline__ cplx_t<T> derive(int code, cplx_t<T> w, int mx, int my, const Geom& g, double ks2,
-                                            double test_lim, T scale, T U) {
+                                            int test_m2max, T scale, T U) {
   using C = cplx_t<T>;
   const int m2 = mx * mx + my * my;
-  if (code & D_TEST) {
-    if (double(m2) * test_lim > double(g.n) * double(g.n)) w = mk<C>(T(0), T(0));
-  }
+  if ((code & D_TEST) && m2 > test_m2max) w = mk<C>(T(0), T(0));
   const T kx = T(g.kscale) * T(mx);
   const T ky = T(g.kscale) * T(my);
   const T ik2 = InvK2<T>::get(ks2, m2);
@@ -78,7 +76,6 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
   const int nt = blockDim.x;
   const int nspec = W * Ny;
   const double ks2 = g.kscale * g.kscale;
-  const double test_lim = 4.0 * d.test_ratio * d.test_ratio;
 
   if (d.flag) {
     const int stop = __syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0);
@@ -90,7 +87,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
   C* jh = reinterpret_cast<C*>(d.jh);
   C* dh = reinterpret_cast<C*>(d.dh);
   const T rpow = T(d.rpow);
-  double hm = 0.0, mm = 0.0;
+  GermanoAcc<T> acc_hm, acc_mm;
 
   // ---- Phase F: forward y-transforms of the incoming mixed arrays
   for (int f = 0; f < d.nfwd; ++f) {
@@ -115,7 +112,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           else slotB[e] = cadd(slotB[e], cmul_ik(X, ky));            // + i ky F[g wy]
           break;
         case CO_DYN_REDUCE: {
-          const bool in_test = double(mx * mx + my * my) * test_lim <= double(N) * double(N);
+          const bool in_test = mx * mx + my * my <= d.test_m2max;
           if (f == 0) {                                              // J
             slotA[e] = X;
             jh[gi] = X;
@@ -132,10 +129,12 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           } else {
             const C M = cadd(slotB[e], cscale(cmul_ik(X, ky), rpow));
             const C H = slotA[e];
-            const double wgt = mx == 0 ? 1.0 : 2.0;
+            const T wgt = mx == 0 ? T(1) : T(2);
             if (mx < g.Kc) {
-              hm += wgt * (double(H.x) * double(M.x) + double(H.y) * double(M.y));
-              mm += wgt * (double(M.x) * double(M.x) + double(M.y) * double(M.y));
+              acc_hm.add_prod(wgt * H.x, M.x);
+              acc_hm.add_prod(wgt * H.y, M.y);
+              acc_mm.add_prod(wgt * M.x, M.x);
+              acc_mm.add_prod(wgt * M.y, M.y);
             }
           }
           break;
@@ -157,6 +156,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
 
   if (d.op == CO_DYN_REDUCE) {
     // deterministic block reduction of the Germano partial sums
+    double hm = acc_hm.value(), mm = acc_mm.value();
     for (int o = 16; o > 0; o >>= 1) {
       hm += __shfl_down_sync(0xffffffffu, hm, o);
       mm += __shfl_down_sync(0xffffffffu, mm, o);
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
       int r = -1;
       if (row <= g.K) r = row;
       else if (row >= N - g.K) r = row - N + Ny;
-      if (r >= 0 && mx < g.Kc) v = derive<T>(code, slotA[(size_t)c * Ny + r], mx, my_of_r(g, r), g, ks2, test_lim, scale, U);
+      if (r >= 0 && mx < g.Kc) v = derive<T>(code, slotA[(size_t)c * Ny + r], mx, my_of_r(g, r), g, ks2, d.test_m2max, scale, U);
       tile[e] = v;
     }
     fft_batched<C>(tile, plan, W, tw, +1);

@@ -15,8 +15,9 @@
 // exchanges are free of bank conflicts.
 //
 // Passes: radix 16 (as 4 x 4 with W16 twiddles) while possible, then one pass
-// of radix 8, 4 or 2.  Twiddles W_N^j come from a table computed on the host
-// from exactly reduced angles.
+// of radix 8, 4 or 2.  Each thread reads its twiddle bases W_N^j once from a
+// table computed on the host from exactly reduced angles and forms the
+// powers it needs in registers.
 #pragma once
 
 #include "fft.cuh"
@@ -84,13 +85,50 @@ template <typename T, int N> struct E16 {
 
   __device__ static __forceinline__ int pad(int i) { return i + (i >> 4); }
 
+  // Twiddle bases of the non-first passes for thread t: a pass of radix R and
+  // span NS multiplies element r of butterfly j by W_N^(r k N/(NS R)),
+  // k = j mod NS, i.e. by the r-th power of base(j) = W_N^(k N/(NS R)).
+  // Bases are loaded once per kernel; powers are formed in registers.
+  static constexpr int NBL = RLAST > 1 ? 16 / RLAST : 1;
+  struct Tw {
+    C p2;        // pass 2 (NS = 16, R = 16)
+    C p3;        // pass 3 (NS = 256, R = 16), N = 4096 only
+    C pl[NBL];   // last pass (R = RLAST), one base per butterfly
+  };
+
+  __device__ static __forceinline__ Tw load_tw(int t, const C* __restrict__ tw) {
+    Tw b;
+    b.p2 = mk<C>(T(1), T(0));
+    b.p3 = mk<C>(T(1), T(0));
+    if constexpr (NP16 >= 2) b.p2 = __ldg(&tw[(t & 15) * (N / 256)]);
+    if constexpr (NP16 >= 3) b.p3 = __ldg(&tw[(t & 255) * (N / 4096)]);
+    if constexpr (RLAST > 1) {
+      constexpr int NS = N / RLAST;
+#pragma unroll
+      for (int bb = 0; bb < NBL; ++bb) b.pl[bb] = __ldg(&tw[((t + TT * bb) & (NS - 1)) * (N / (NS * RLAST))]);
+    }
+    return b;
+  }
+
+  // w^r for r = 1 .. R-1 by a product tree of depth <= log2(R): squares for
+  // powers of two, w^hb * w^(r - hb) otherwise (hb = largest power of two < r).
+  template <int R>
+  __device__ static __forceinline__ void powers(C w, C* pw, int sign) {
+    if (sign > 0) w.y = -w.y;
+    pw[1] = w;
+#pragma unroll
+    for (int r = 2; r < R; ++r) {
+      int hb = 1;
+      while (hb * 2 <= r) hb *= 2;
+      pw[r] = (hb == r) ? cmul(pw[r / 2], pw[r / 2]) : cmul(pw[hb], pw[r - hb]);
+    }
+  }
+
   // One Stockham pass; x in natural ownership on entry.  Non-last passes
-  // exchange through buf (stride `cs` complex between consecutive padded
-  // slots' owners is 1; `buf` already points at this sequence's slot area).
+  // exchange through buf (this sequence's padded slot area).
   template <int R, int NS, bool LAST>
-  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* __restrict__ tw, int sign) {
+  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* base, int sign) {
     constexpr int NB = 16 / R;
-    constexpr int TWS = N / (NS * R);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = t + TT * b;
@@ -99,21 +137,19 @@ template <typename T, int N> struct E16 {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = x[b + NB * r];
       if constexpr (NS > 1) {
+        C pw[R];
+        powers<R>(base[b], pw, sign);
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w = __ldg(&tw[r * k * TWS]);
-          if (sign > 0) w.y = -w.y;
-          v[r] = cmul(v[r], w);
-        }
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], pw[r]);
       }
       dftR<C, R>(v, sign);
       if constexpr (LAST) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[b + NB * r] = v[r];
       } else {
-        const int base = (j / NS) * NS * R + k;
+        const int base_i = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad(base + NS * r)] = v[r];
+        for (int r = 0; r < R; ++r) buf[pad(base_i + NS * r)] = v[r];
       }
     }
     if constexpr (!LAST) {
@@ -123,33 +159,35 @@ template <typename T, int N> struct E16 {
     }
   }
 
-  // Full transform.  bufs[0], bufs[1] alternate per exchange (ph toggles);
-  // callers pass the same ph through every use of the two buffers.
-  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const C* __restrict__ tw, int sign) {
+  // Full transform.  b0, b1 alternate per exchange (ph toggles); callers
+  // pass the same ph through every use of the two buffers.
+  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const Tw& tw, int sign) {
     if constexpr (NP16 >= 1) {
       constexpr bool last = (NP16 == 1 && RLAST == 1);
-      pass<16, 1, last>(x, t, ph ? b1 : b0, tw, sign);
+      pass<16, 1, last>(x, t, ph ? b1 : b0, nullptr, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (NP16 >= 2) {
       constexpr bool last = (NP16 == 2 && RLAST == 1);
-      pass<16, 16, last>(x, t, ph ? b1 : b0, tw, sign);
+      pass<16, 16, last>(x, t, ph ? b1 : b0, &tw.p2, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (NP16 >= 3) {
       constexpr bool last = (NP16 == 3 && RLAST == 1);
-      pass<16, 256, last>(x, t, ph ? b1 : b0, tw, sign);
+      pass<16, 256, last>(x, t, ph ? b1 : b0, &tw.p3, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (RLAST > 1) {
       constexpr int NS = N / RLAST;
-      pass<RLAST, NS, true>(x, t, ph ? b1 : b0, tw, sign);
+      pass<RLAST, NS, true>(x, t, ph ? b1 : b0, tw.pl, sign);
     }
   }
 };
 
 }  // namespace fast
 
+// k_x columns per CTA of the specialised column pass
+template <int N> int fast_col_width();
 template <typename T, int N>
 cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st);
 template <typename T, int N>

@@ -7,6 +7,22 @@
 #include "fast.cuh"
 #include "qg_kernels.h"
 
+#ifndef QG_ROW_MINB
+#define QG_ROW_MINB 4
+#endif
+#ifndef QG_COL_MINB
+#define QG_COL_MINB 2
+#endif
+#ifndef QG_COL_MINB_REDUCE
+#define QG_COL_MINB_REDUCE 1
+#endif
+#ifndef QG_COL_MINB_FWD
+#define QG_COL_MINB_FWD 1
+#endif
+#ifndef QG_COL_MINB_CURL
+#define QG_COL_MINB_CURL 2
+#endif
+
 namespace qg {
 namespace fast {
 
@@ -15,12 +31,25 @@ template <int N> struct RowCfg {
   static constexpr int ROWS = TT >= 128 ? 1 : 128 / TT;
   static constexpr int THREADS = TT * ROWS;
 };
+// resident CTAs per SM requested from the register allocator (FP32; FP64 takes 1)
+template <typename T, int OP = -1> struct Occ {
+  static constexpr int row = QG_ROW_MINB;
+  static constexpr int col = OP == CO_DYN_REDUCE ? QG_COL_MINB_REDUCE
+                             : OP == CO_FORWARD ? QG_COL_MINB_FWD
+                             : OP == CO_CURL    ? QG_COL_MINB_CURL
+                                                : QG_COL_MINB;
+};
+template <int OP> struct Occ<double, OP> { static constexpr int row = 1, col = 1; };
 
+#ifndef QG_COL_W
+#define QG_COL_W 2
+#endif
 template <int N> struct ColCfg {
-  static constexpr int W = 2;  // k_x columns per CTA
+  static constexpr int W = QG_COL_W;  // k_x columns per CTA
   static constexpr int TT = N / 16;
   static constexpr int THREADS = W * TT;
-  static constexpr int CP = N + N / 16 + 8;  // column stride in shared memory (complex); = 8 mod 16
+  // column stride in shared memory (complex elements): 16 / W mod 16 keeps the exchanges conflict-free
+  static constexpr int CP = N + N / 16 + 16 / W;
 };
 
 template <typename T>
@@ -51,7 +80,7 @@ struct RowCtx {
   C* b0;
   C* b1;
   int ph;
-  const C* tw;
+  typename E::Tw tw;
   const Geom* g;
   int bad;
 
@@ -164,7 +193,7 @@ __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, c
 }
 
 template <typename T, int N, int PROG>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) row_fast_kernel(Geom g, RowDesc d,
+__global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kernel(Geom g, RowDesc d,
                                                                        const cplx_t<T>* __restrict__ tw) {
   using E = E16<T, N>;
   using C = cplx_t<T>;
@@ -178,7 +207,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) row_fast_kernel(Geom g, Ro
   cx.b0 = sm + (size_t)(2 * lr) * E::BUF;
   cx.b1 = cx.b0 + E::BUF;
   cx.ph = 0;
-  cx.tw = tw;
+  cx.tw = E::load_tw(cx.t, tw);
   cx.g = &g;
   cx.bad = 0;
   if (d.flag) {
@@ -265,33 +294,8 @@ template <> struct FInvK2<float> {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ cplx_t<T> fderive(int code, cplx_t<T> w, int mx, int my, double kscale, double ks2,
-                                             double test_lim, double n2, T scale, T U) {
-  using C = cplx_t<T>;
-  const int m2 = mx * mx + my * my;
-  if ((code & D_TEST) && double(m2) * test_lim > n2) w = mk<C>(T(0), T(0));
-  const T kx = T(kscale) * T(mx);
-  const T ky = T(kscale) * T(my);
-  const T ik2 = FInvK2<T>::get(ks2, m2);
-  const C psi = mk<C>(-w.x * ik2, -w.y * ik2);
-  C v;
-  switch (code & 7) {
-    case D_U: v = cmul_ik(psi, -ky); break;
-    case D_V: v = cmul_ik(psi, kx); break;
-    case D_WX: v = cmul_ik(w, kx); break;
-    case D_WY: v = cmul_ik(w, ky); break;
-    case D_PXY: v = cscale(psi, -(kx * ky)); break;
-    case D_PD: v = cscale(psi, -(kx * kx - ky * ky)); break;
-    default: v = w; break;
-  }
-  v = cscale(v, scale);
-  if ((code & 7) == D_U && m2 == 0) v = mk<C>(U, T(0));
-  return v;
-}
-
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, ColDesc d,
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(Geom g, ColDesc d,
                                                                        const cplx_t<T>* __restrict__ tw) {
   using E = E16<T, N>;
   using C = cplx_t<T>;
@@ -310,11 +314,11 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
   C* b0 = sm + c * CP;
   C* b1 = sm + (W + c) * CP;
   int ph = 0;
+  const typename E::Tw twb = E::load_tw(t, tw);
   if (d.flag) {
     if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
   }
   const double ks2 = g.kscale * g.kscale;
-  const double test_lim = 4.0 * d.test_ratio * d.test_ratio;
   const double n2 = double(N) * double(N);
   const T kxv = T(g.kscale) * T(mx);
   C* w0 = reinterpret_cast<C*>(d.w0);
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
   const size_t colbase = (size_t)mx * g.SP;
 
   C x[16], A[16], B[16];
-  double hm = 0.0, mm = 0.0;
+  GermanoAcc<T> acc_hm, acc_mm;
 
   // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
   if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
       const C* src = reinterpret_cast<const C*>(d.fin[f]) + mx;
 #pragma unroll
       for (int m = 0; m < 16; ++m) x[m] = src[(size_t)(t + TT * m) * g.IP];
-      E::run(x, t, b0, b1, ph, tw, -1);
+      E::run(x, t, b0, b1, ph, twb, -1);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k = t + TT * m;
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
         } else if constexpr (OP == CO_DYN_REDUCE) {
           const bool kept = k <= K || k >= N - K;
           const int r = k <= K ? k : k - N + Ny;
-          const bool in_test = double(mx * mx + my * my) * test_lim <= n2;
+          const bool in_test = mx * mx + my * my <= d.test_m2max;
           if (f == 0) {
             A[m] = X;
             if (kept) jh[colbase + r] = X;
@@ -365,9 +369,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
             const C M = cadd(B[m], cscale(cmul_ik(X, ky), T(d.rpow)));
             const C H = A[m];
             if (kept && col_ok) {
-              const double wgt = mx == 0 ? 1.0 : 2.0;
-              hm += wgt * (double(H.x) * double(M.x) + double(H.y) * double(M.y));
-              mm += wgt * (double(M.x) * double(M.x) + double(M.y) * double(M.y));
+              // weight 2 for k_x > 0 (the conjugate half), applied exactly
+              const T wgt = mx == 0 ? T(1) : T(2);
+              acc_hm.add_prod(wgt * H.x, M.x);
+              acc_hm.add_prod(wgt * H.y, M.y);
+              acc_mm.add_prod(wgt * M.x, M.x);
+              acc_mm.add_prod(wgt * M.y, M.y);
             }
           }
         } else if constexpr (OP == CO_CURL) {
@@ -381,6 +388,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
   }
 
   if constexpr (OP == CO_DYN_REDUCE) {
+    double hm = acc_hm.value(), mm = acc_mm.value();
     for (int o = 16; o > 0; o >>= 1) {
       hm += __shfl_down_sync(0xffffffffu, hm, o);
       mm += __shfl_down_sync(0xffffffffu, mm, o);
@@ -472,20 +480,68 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) col_fast_kernel(Geom g, Co
       A[m] = wn;
     }
 
-    // ---- derived fields, inverse y-transforms, mixed arrays out
+    // ---- derived fields, inverse y-transforms, mixed arrays out.
+    // Per owned mode: the state scaled by 1/N^2 (so the two inverse passes
+    // return physical values), 1/|k|^2, and masks of the kept 2/3 band and of
+    // the test filter; each derived field then costs a few operations per mode.
     const T scale = T(1.0 / n2);
-    const T U = T(d.U);
+    T ik2[16];
+    unsigned keep = 0u, intest = 0u;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = t + TT * m;
+      const int my = k <= K ? k : k - N;
+      const int m2 = mx * mx + my * my;
+      if ((k <= K || k >= N - K) && col_ok) keep |= 1u << m;
+      if (m2 <= d.test_m2max) intest |= 1u << m;
+      ik2[m] = FInvK2<T>::get(ks2, m2);
+      A[m] = cscale(A[m], scale);
+    }
+    const T ksc = T(g.kscale);
 #pragma unroll 1
     for (int q = 0; q < d.nder; ++q) {
       const int code = d.der[q];
+      const unsigned on = (code & D_TEST) ? (keep & intest) : keep;
+      C w[16];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int k = t + TT * m;
-        const bool kept = (k <= K || k >= N - K) && col_ok;
-        const int my = k <= K ? k : k - N;
-        x[m] = kept ? fderive<T>(code, A[m], mx, my, g.kscale, ks2, test_lim, n2, scale, U) : mk<C>(T(0), T(0));
+      for (int m = 0; m < 16; ++m) w[m] = ((on >> m) & 1u) ? A[m] : mk<C>(T(0), T(0));
+#define QG_KY(m) (ksc * T((t + TT * (m)) <= K ? (t + TT * (m)) : (t + TT * (m)) - N))
+      switch (code & 7) {
+        case D_U:  // -i ky psi, psi = -w / |k|^2
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(cscale(w[m], ik2[m]), QG_KY(m));
+          if (mx == 0 && t == 0) x[0] = mk<C>(T(d.U), T(0));
+          break;
+        case D_V:  // i kx psi
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(cscale(w[m], -ik2[m]), kxv);
+          break;
+        case D_WX:
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(w[m], kxv);
+          break;
+        case D_WY:
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(w[m], QG_KY(m));
+          break;
+        case D_PXY:  // -kx ky psi = kx ky w / |k|^2
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = cscale(w[m], kxv * QG_KY(m) * ik2[m]);
+          break;
+        case D_PD:  // -(kx^2 - ky^2) psi = (kx^2 - ky^2) w / |k|^2
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const T ky = QG_KY(m);
+            x[m] = cscale(w[m], (kxv * kxv - ky * ky) * ik2[m]);
+          }
+          break;
+        default:
+#pragma unroll
+          for (int m = 0; m < 16; ++m) x[m] = w[m];
+          break;
       }
-      E::run(x, t, b0, b1, ph, tw, +1);
+#undef QG_KY
+      E::run(x, t, b0, b1, ph, twb, +1);
       C* dst = reinterpret_cast<C*>(d.dout[q]) + mx;
 #pragma unroll
       for (int m = 0; m < 16; ++m) dst[(size_t)(t + TT * m) * g.IP] = x[m];
@@ -570,6 +626,7 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cud
 }
 
 #define QG_INSTANTIATE_FAST(N)                                                                          \
+  template <> int fast_col_width<N>() { return fast::ColCfg<N>::W; }                                    \
   template cudaError_t launch_row_fast<float, N>(const Geom&, const RowDesc&, const void*, cudaStream_t);  \
   template cudaError_t launch_row_fast<double, N>(const Geom&, const RowDesc&, const void*, cudaStream_t); \
   template cudaError_t launch_col_fast<float, N>(const Geom&, const ColDesc&, const void*, cudaStream_t);  \

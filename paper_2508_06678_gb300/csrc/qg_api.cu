@@ -128,6 +128,7 @@ struct qg_handle {
   bool fast = false;  // power-of-two grid served by the register-resident FFT kernels
   bool dynamic = false;
   double static_coeff = 0.0;
+  int test_m2max = 0;  // largest |m|^2 the test filter keeps
   // stage program
   int row_prog = RP_NONE, nin = 4, nout = 1;
   unsigned dx_mask = 0;
@@ -296,6 +297,7 @@ ColDesc col_base(qg_handle* h) {
   d.U = h->U;
   d.coeff = h->static_coeff;
   d.test_ratio = h->cl.test_ratio;
+  d.test_m2max = h->test_m2max;
   const int p = (h->cl.kind == QG_SMAG || h->cl.kind == QG_DSMAG) ? 2 : 3;
   d.closure_pow = p;
   d.rpow = std::pow(h->cl.test_ratio, p);
@@ -481,6 +483,14 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   h->par = *params;
   h->dynamic = closure->kind == QG_DSMAG || closure->kind == QG_DLEITH;
   const double delta = grid->L / n;
+  {
+    // |m|^2 (2r)^2 <= N^2, evaluated in FP64 for every integer |m|^2 of the 2/3 band
+    const double r2 = (2.0 * closure->test_ratio) * (2.0 * closure->test_ratio);
+    const int kmax = (n - 1) / 3;
+    int m2 = 0;
+    while (m2 + 1 <= 2 * kmax * kmax && double(m2 + 1) * r2 <= double(n) * double(n)) ++m2;
+    h->test_m2max = m2;
+  }
   if (closure->kind == QG_SMAG) h->static_coeff = std::pow(closure->c * delta, 2);
   if (closure->kind == QG_LEITH) h->static_coeff = std::pow(closure->c * delta, 3);
 
@@ -556,11 +566,19 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   // power-of-two grids use the register-resident kernels (two k_x columns per CTA)
   {
     const bool pow2 = (n & (n - 1)) == 0 && n >= 256 && n <= 4096;
-    const size_t fast_col_smem = (size_t)2 * 2 * (n + n / 16 + 8) * csz;
+    int fw = 2;
+    switch (n) {
+      case 256: fw = fast_col_width<256>(); break;
+      case 512: fw = fast_col_width<512>(); break;
+      case 1024: fw = fast_col_width<1024>(); break;
+      case 2048: fw = fast_col_width<2048>(); break;
+      case 4096: fw = fast_col_width<4096>(); break;
+    }
+    const size_t fast_col_smem = (size_t)2 * fw * (n + n / 16 + 16 / fw) * csz;
     const size_t fast_row_smem = (size_t)2 * (n >= 2048 ? 1 : 2048 / n) * (n + n / 16) * csz;
     h->fast = pow2 && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
     if (getenv("QG_FORCE_GENERIC")) h->fast = false;
-    if (h->fast) h->W = 2;
+    if (h->fast) h->W = fw;
   }
   g.Kcp = (g.Kc + h->W - 1) / h->W * h->W;
   g.IP = g.Kcp;

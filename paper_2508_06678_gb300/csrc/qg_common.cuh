@@ -139,6 +139,7 @@ struct ColDesc {
   double coeff;     // static closure coefficient C
   int closure_pow;  // p of r^p in the Germano M
   double test_ratio;
+  int test_m2max;   // test filter keeps |m|^2 <= test_m2max (exact integer form of |m| <= N / (2 r))
   double rpow;      // r^p
   // Germano partial sums: written by CO_DYN_REDUCE (2 doubles per block), read by CO_DYN_COMBINE
   double* partials;
@@ -148,6 +149,33 @@ struct ColDesc {
   const void* visc_y;  // exp(-nu ky^2 dt), per r
   double visc_mu;      // exp(-mu dt)
   int* flag;
+};
+
+// Per-thread accumulator of the Germano sums.  FP64 fields accumulate in
+// FP64; FP32 fields use error-free transformations (TwoProduct by FMA,
+// TwoSum) so the per-thread partial carries about twice FP32 precision
+// before it joins the FP64 cross-thread reduction.
+template <typename T> struct GermanoAcc;
+template <> struct GermanoAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct GermanoAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float h = a * b;
+    const float l = fmaf(a, b, -h);
+    add(h);
+    c += l;
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
 };
 
 }  // namespace qg
