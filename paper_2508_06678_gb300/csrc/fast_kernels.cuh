@@ -7,6 +7,9 @@
 #include "fast.cuh"
 #include "qg_kernels.h"
 
+#ifndef QG_PREFETCH
+#define QG_PREFETCH 1
+#endif
 #ifndef QG_ROW_MINB
 #define QG_ROW_MINB 4
 #endif
@@ -332,11 +335,30 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
 
   // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
   if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
+#if QG_PREFETCH
+    C xn[16];
+    {
+      const C* src = reinterpret_cast<const C*>(d.fin[0]) + mx;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) xn[m] = src[(size_t)(t + TT * m) * g.IP];
+    }
+#endif
 #pragma unroll 1
     for (int f = 0; f < d.nfwd; ++f) {
+#if QG_PREFETCH
+      // field f arrived in xn; start loading field f + 1 before transforming f
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = xn[m];
+      if (f + 1 < d.nfwd) {
+        const C* nsrc = reinterpret_cast<const C*>(d.fin[f + 1]) + mx;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) xn[m] = nsrc[(size_t)(t + TT * m) * g.IP];
+      }
+#else
       const C* src = reinterpret_cast<const C*>(d.fin[f]) + mx;
 #pragma unroll
       for (int m = 0; m < 16; ++m) x[m] = src[(size_t)(t + TT * m) * g.IP];
+#endif
       E::run(x, t, b0, b1, ph, twb, -1);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
