@@ -177,6 +177,33 @@ int qg_profile(qg_handle* h, int32_t enable);
  * launches.  Synchronises the handle's stream.  nclass <= QG_NUM_KCLASS. */
 int qg_kernel_times(qg_handle* h, int32_t* counts, double* ms, int32_t nclass);
 
+/* Energy, enstrophy, max |w| and finiteness of a physical vorticity field,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc where they need
+ * these numbers, such as hosts whose framework owns all device memory through
+ * its own allocator or a fixed budget, code that must not introduce the
+ * device-wide synchronisation an allocation can cause, and real-time loops
+ * that must not pay for or risk an allocation.
+ *   omega: N*N device array of dtype (QG_FP32 = float, QG_FP64 = double),
+ *          row-major [y][x]; read only.  The field is projected as by
+ *          qg_set_state (2/3 band, zero mean) and the statistics are those
+ *          qg_diagnostics reports for that state, computed in dtype with FP64
+ *          sums.
+ *   n: grid size, even, 2^a 3^b, 16 <= n <= 512;  L: box length (> 0).
+ *   cuda_stream: cudaStream_t (as void*) the work is enqueued on; the call is
+ *          asynchronous.
+ *   stats: 4 device doubles (output): energy, enstrophy, max |w|, finite
+ *          (1.0 or 0.0).
+ * Scratch lives in one static device array of 5 MiB that every GPU loading
+ * the library holds until the process exits.  All calls share it and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: QG_ERR_ARG for n > 512 or other bad
+ * arguments (nothing is enqueued), QG_ERR_CUDA. */
+int qg_field_stats_static(const void* omega, int32_t n, double L, int32_t dtype, void* cuda_stream, double* stats);
+
 /* Thread-local description of the last error (never NULL). */
 const char* qg_last_error(void);
 

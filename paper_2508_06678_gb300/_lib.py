@@ -64,6 +64,7 @@ SIGNATURES = {
                                  C.POINTER(qg_params), C.c_double, C.c_double, C.c_int32, DP, DP, DP, DP]),
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int32]),
+    "qg_field_stats_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
     "qg_last_error": (C.c_char_p, []),
     "qg_version": (C.c_char_p, []),
 }

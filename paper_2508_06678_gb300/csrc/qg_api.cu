@@ -113,6 +113,11 @@ void cos_sin_frac(long j, long n, double* c, double* s) {
 
 }  // namespace
 
+namespace qg {
+// Lets other translation units of the library report through qg_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace qg
+
 struct qg_handle {
   Geom g{};
   int fp32 = 0;

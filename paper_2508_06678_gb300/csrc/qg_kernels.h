@@ -24,6 +24,9 @@ template <typename T>
 cudaError_t launch_phys_maxabs(const Geom& g, const void* f, double* partials, int nblk, double* out,
                                cudaStream_t st);
 
+// Sets the thread-local message returned by qg_last_error().
+void set_last_error(const char* msg);
+
 // Element-wise precision conversion between device buffers.
 cudaError_t launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, size_t count, cudaStream_t st);
 
