@@ -348,7 +348,9 @@ def apriori_filter(ops_f: Ops, fh: np.ndarray, n_c: int, gaussian: bool = True) 
     d_ff = L / n_c
     k2 = ops_f.k2
     h = np.exp(-k2 * d_ff ** 2 / 6.0) if gaussian else np.ones_like(k2)
-    h = h * (k2 <= (math.pi / d_ff) ** 2)
+    # |k| <= pi / Delta_FF  <=>  |m| <= N_c / 2 for integer wavenumbers m, tested exactly
+    m2 = ops_f.mx ** 2 + ops_f.my ** 2
+    h = h * (4.0 * m2 <= float(n_c) ** 2)
     fh = fh * h
     out = np.zeros((n_c, n_c // 2 + 1), dtype=np.complex128)
     half = n_c // 2
