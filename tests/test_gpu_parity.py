@@ -218,3 +218,63 @@ def test_fast_and_generic_kernels_agree(kind, prec, tol, monkeypatch):
             s.step(10)
             out.append(s.get_state())
     assert rel(out[0], out[1]) < tol
+
+
+# --------------------------------------------------------------------------
+# A priori SGS analysis (Sec. III, Eq. 5-8, 15) through qg_sgs_apriori
+# --------------------------------------------------------------------------
+
+def _apriori_pair(n_fr, n_les, kind, seed=4, gaussian=True):
+    L = 2 * math.pi
+    w = S.init_field(seed, n_fr, k_peak=n_fr / 10)
+    chi = S.island_mask(n_fr, radius=0.8)
+    chs = S.sponge_mask(n_fr)
+    cl = O.Closure(kind, c=0.2)
+    pr = O.Params()
+    ref = O.sgs_apriori(w, n_les, L, chi, chs, cl, pr, 0.5, 5.0, gaussian=gaussian)
+    from paper_2508_06678_gb300._lib import qg_closure, qg_params
+    got = qg.qg_sgs_apriori(w, n_les, L, chi, chs, qg_closure(kind, 0, 0.2, 2.0),
+                            qg_params(pr.dt, pr.nu, pr.mu, pr.eta, pr.sponge_rate), 0.5, 5.0,
+                            0 if gaussian else 1)
+    return ref, got
+
+
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+@pytest.mark.parametrize("sizes", [(128, 64), (96, 48), (192, 64)])
+def test_apriori_parity(kind, sizes):
+    ref, got = _apriori_pair(*sizes, kind)
+    pe, pm, parts, r = got
+    assert rel(pe, ref[0]) < 1e-10
+    for i in range(3):
+        if np.linalg.norm(ref[2][i]) > 0:
+            assert rel(parts[i], ref[2][i]) < 1e-10
+    if kind == S.NONE:
+        assert np.all(pm == 0) and math.isnan(r)
+    elif math.isnan(ref[3]):
+        assert np.linalg.norm(pm) == 0 or math.isnan(r)
+    else:
+        assert rel(pm, ref[1]) < 1e-9
+        assert abs(r - ref[3]) < 1e-9
+
+
+def test_apriori_no_gaussian_flag():
+    ref, got = _apriori_pair(128, 64, S.LEITH, gaussian=False)
+    assert rel(got[0], ref[0]) < 1e-10
+    assert abs(got[3] - ref[3]) < 1e-9
+
+
+def test_apriori_full_size_2048_to_512():
+    """The configuration's a priori check: a 2048^2 field filtered to 512^2."""
+    ref, got = _apriori_pair(2048, 512, S.DLEITH, seed=5)
+    assert rel(got[0], ref[0]) < 1e-10
+    if not math.isnan(ref[3]):
+        assert abs(got[3] - ref[3]) < 1e-8
+
+
+def test_apriori_rejects_unsupported_sizes():
+    from paper_2508_06678_gb300._lib import qg_closure, qg_params
+    w = S.init_field(0, 64)
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_sgs_apriori(w, 64, 2 * math.pi, None, None, qg_closure(1, 0, 0.2, 2.0),
+                          qg_params(2e-3, 5e-3, 0.0, 1e-3, 50.0), 0.5, 5.0)
+    assert ei.value.code == qg.QG_ERR_UNSUPPORTED
