@@ -98,10 +98,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_id: str):
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
-        self.gpu = gpu_index
+        self.gpu = gpu_id
 
     def start(self):
         try:
@@ -189,13 +189,16 @@ def run_reference(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=1000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="island2048-dleith", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 throughput / error leg")
+    ap.add_argument("--fp64-steps", type=int, default=50)
+    ap.add_argument("--err-steps", type=int, default=100)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]()
     if args.impl == "reference":
@@ -233,11 +236,14 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # ---- timed region: K steps on device-resident state, per-kernel events on
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    # ---- timed region: K steps on device-resident state
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except (AttributeError, RuntimeError):
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
     qg_h = solver.h
-    lib.qg_profile(qg_h, 1)
     sampler.start()
     time.sleep(0.3)
     barrier()
@@ -251,17 +257,26 @@ def main():
     barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    counts = (C.c_int32 * 8)()
-    kms = (C.c_double * 8)()
-    lib.qg_kernel_times(qg_h, counts, kms, 8)
-    lib.qg_profile(qg_h, 0)
     solver.sync()
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * wl.n * wl.n * args.steps / (ms / 1e3)
-    launches = int(sum(counts))
+
+    # ---- per-kernel durations: a second pass of the same K steps with a CUDA
+    # event pair recorded around every launch on the solver's stream (the
+    # brackets add a few per cent to the step, so the value above is taken
+    # without them)
+    lib.qg_profile(qg_h, 1)
+    torch.cuda.synchronize()
+    solver.step(args.steps)
+    counts = (C.c_int32 * 8)()
+    kms = (C.c_double * 8)()
+    lib.qg_kernel_times(qg_h, counts, kms, 8)
+    lib.qg_profile(qg_h, 0)
+    solver.sync()
+    launches = int(sum(counts))  # our kernels per K-step pass (the timed pass launches the same)
 
     # ---- roofline of the dominant kernel class
     peaks, peak_src = measured_peaks()
@@ -275,19 +290,21 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     step_bytes = sum(a * b for a, b in model.values())
     traffic = None
-    prof_path = os.path.join(ROOT, "profiles", f"traffic_{wl.name}_{args.precision}.json")
+    prof_path = os.path.join(ROOT, "profiles", f"row_pass_{wl.name}_{args.precision}.md")
     if os.path.exists(prof_path):
-        try:
-            rec = json.load(open(prof_path))
-            if rec.get("kernel_class") == dom:
-                traffic = rec.get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+        rec = {}
+        for line in open(prof_path):
+            if ":" in line and line.split(":")[0].startswith("traffic_"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("traffic_kernel_class") == dom and rec.get("traffic_bytes_per_launch"):
+            traffic = int(rec["traffic_bytes_per_launch"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "peak_source": peak_src,
                 "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
                 "step_model_bytes": step_bytes,
-                "step_frac": step_bytes / (ms / 1e3 / args.steps) / 1e9 / peak}
+                "step_frac": step_bytes / (ms / 1e3 / args.steps) / 1e9 / peak,
+                "measured_in": "CUDA events around each launch, second pass of the same K steps"}
 
     # ---- end to end through the public API with host buffers
     torch.cuda.synchronize()
@@ -313,6 +330,40 @@ def main():
            "d2h_bytes_per_step": (wl.n * wl.n * esz + 56) / args.steps,
            "api": "qg_set_state(host) + qg_step(K) + qg_get_state(host) + qg_diagnostics"}
 
+    # ---- the FP64 form on the same workload: throughput, and the FP32 form's
+    # relative vorticity error against it after the same number of steps
+    fp64 = None
+    if fp32 and not args.no_fp64:
+        s64 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP64, stream=stream)
+        s64.set_state(w0)
+        s64.step(5)
+        s64.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k64 = args.fp64_steps
+        e0.record(stream)
+        s64.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        s32 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32, stream=stream)
+        s64.set_state(w0)
+        s32.set_state(w0)
+        s64.step(args.err_steps)
+        s32.step(args.err_steps)
+        a = s64.get_state()
+        b = s32.get_state()
+        rel_err = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+        d64 = s64.diagnostics()
+        d32 = s32.diagnostics()
+        s32.close()
+        s64.close()
+        fp64 = {"value": wl.n * wl.n / (ms64 / 1e3), "ms_per_step": ms64, "steps_timed": k64,
+                "fp32_speedup": ms64 / (ms / args.steps),
+                "fp32_rel_l2_err_vs_fp64": rel_err, "err_steps": args.err_steps,
+                "energy_rel_diff": abs(d32["energy"] - d64["energy"]) / abs(d64["energy"]),
+                "enstrophy_rel_diff": abs(d32["enstrophy"] - d64["enstrophy"]) / abs(d64["enstrophy"])}
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -331,7 +382,7 @@ def main():
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set > 126 MB L2 (inputs larger than L2, no flush)",
                        "final_energy": diag["energy"], "final_coeff": diag["coeff"], "finite": diag["finite"]},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
             "kernel_ms": {k: v[1] for k, v in per_class.items() if v[0]},
             "kernel_launches": {k: v[0] for k, v in per_class.items() if v[0]},
             "clocks": clocks,

@@ -15,9 +15,8 @@
 // exchanges are free of bank conflicts.
 //
 // Passes: radix 16 (as 4 x 4 with W16 twiddles) while possible, then one pass
-// of radix 8, 4 or 2.  Each thread reads its twiddle bases W_N^j once from a
-// table computed on the host from exactly reduced angles and forms the
-// powers it needs in registers.
+// of radix 8, 4 or 2.  Twiddles come from per-pass tables computed on the host
+// from exactly reduced angles (see pass()).
 #pragma once
 
 #include "fft.cuh"
@@ -85,49 +84,21 @@ template <typename T, int N> struct E16 {
 
   __device__ static __forceinline__ int pad(int i) { return i + (i >> 4); }
 
-  // Twiddle bases of the non-first passes for thread t: a pass of radix R and
-  // span NS multiplies element r of butterfly j by W_N^(r k N/(NS R)),
-  // k = j mod NS, i.e. by the r-th power of base(j) = W_N^(k N/(NS R)).
-  // Bases are loaded once per kernel; powers are formed in registers.
-  static constexpr int NBL = RLAST > 1 ? 16 / RLAST : 1;
-  struct Tw {
-    C p2;        // pass 2 (NS = 16, R = 16)
-    C p3;        // pass 3 (NS = 256, R = 16), N = 4096 only
-    C pl[NBL];   // last pass (R = RLAST), one base per butterfly
-  };
-
-  __device__ static __forceinline__ Tw load_tw(int t, const C* __restrict__ tw) {
-    Tw b;
-    b.p2 = mk<C>(T(1), T(0));
-    b.p3 = mk<C>(T(1), T(0));
-    if constexpr (NP16 >= 2) b.p2 = __ldg(&tw[(t & 15) * (N / 256)]);
-    if constexpr (NP16 >= 3) b.p3 = __ldg(&tw[(t & 255) * (N / 4096)]);
-    if constexpr (RLAST > 1) {
-      constexpr int NS = N / RLAST;
-#pragma unroll
-      for (int bb = 0; bb < NBL; ++bb) b.pl[bb] = __ldg(&tw[((t + TT * bb) & (NS - 1)) * (N / (NS * RLAST))]);
-    }
-    return b;
-  }
-
-  // w^r for r = 1 .. R-1 by a product tree of depth <= log2(R): squares for
-  // powers of two, w^hb * w^(r - hb) otherwise (hb = largest power of two < r).
-  template <int R>
-  __device__ static __forceinline__ void powers(C w, C* pw, int sign) {
-    if (sign > 0) w.y = -w.y;
-    pw[1] = w;
-#pragma unroll
-    for (int r = 2; r < R; ++r) {
-      int hb = 1;
-      while (hb * 2 <= r) hb *= 2;
-      pw[r] = (hb == r) ? cmul(pw[r / 2], pw[r / 2]) : cmul(pw[hb], pw[r - hb]);
-    }
-  }
+  // Twiddles of the non-first passes come from per-pass tables laid out
+  // [r - 1][k] (k fastest): a pass of radix R and span NS multiplies element r
+  // of butterfly j by W_N^(r k N / (NS R)), k = j mod NS, stored at
+  // off + (r - 1) NS + k.  For fixed r the threads of a warp read consecutive
+  // k, so every load touches one or two cache lines, and the values are the
+  // correctly rounded table entries.
+  static constexpr int OFF2 = 0;                                   // pass 2: NS = 16, R = 16
+  static constexpr int OFF3 = NP16 >= 2 ? 15 * 16 : 0;             // pass 3: NS = 256, R = 16 (N = 4096)
+  static constexpr int OFFL = OFF3 + (NP16 >= 3 ? 15 * 256 : 0);   // last pass: NS = N / RLAST, R = RLAST
+  static constexpr int TABLE = OFFL + (RLAST > 1 ? (RLAST - 1) * (N / RLAST) : 0);
 
   // One Stockham pass; x in natural ownership on entry.  Non-last passes
   // exchange through buf (this sequence's padded slot area).
-  template <int R, int NS, bool LAST>
-  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* base, int sign) {
+  template <int R, int NS, bool LAST, int OFF>
+  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* __restrict__ ptw, int sign) {
     constexpr int NB = 16 / R;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -137,10 +108,12 @@ template <typename T, int N> struct E16 {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = x[b + NB * r];
       if constexpr (NS > 1) {
-        C pw[R];
-        powers<R>(base[b], pw, sign);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], pw[r]);
+        for (int r = 1; r < R; ++r) {
+          C w = __ldg(&ptw[OFF + (r - 1) * NS + k]);
+          if (sign > 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
       }
       dftR<C, R>(v, sign);
       if constexpr (LAST) {
@@ -161,25 +134,26 @@ template <typename T, int N> struct E16 {
 
   // Full transform.  b0, b1 alternate per exchange (ph toggles); callers
   // pass the same ph through every use of the two buffers.
-  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const Tw& tw, int sign) {
+  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const C* __restrict__ ptw,
+                                             int sign) {
     if constexpr (NP16 >= 1) {
       constexpr bool last = (NP16 == 1 && RLAST == 1);
-      pass<16, 1, last>(x, t, ph ? b1 : b0, nullptr, sign);
+      pass<16, 1, last, 0>(x, t, ph ? b1 : b0, ptw, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (NP16 >= 2) {
       constexpr bool last = (NP16 == 2 && RLAST == 1);
-      pass<16, 16, last>(x, t, ph ? b1 : b0, &tw.p2, sign);
+      pass<16, 16, last, OFF2>(x, t, ph ? b1 : b0, ptw, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (NP16 >= 3) {
       constexpr bool last = (NP16 == 3 && RLAST == 1);
-      pass<16, 256, last>(x, t, ph ? b1 : b0, &tw.p3, sign);
+      pass<16, 256, last, OFF3>(x, t, ph ? b1 : b0, ptw, sign);
       if (!last) ph ^= 1;
     }
     if constexpr (RLAST > 1) {
       constexpr int NS = N / RLAST;
-      pass<RLAST, NS, true>(x, t, ph ? b1 : b0, tw.pl, sign);
+      pass<RLAST, NS, true, OFFL>(x, t, ph ? b1 : b0, ptw, sign);
     }
   }
 };
@@ -188,6 +162,11 @@ template <typename T, int N> struct E16 {
 
 // k_x columns per CTA of the specialised column pass
 template <int N> int fast_col_width();
+// complex entries of the per-pass twiddle table of the specialised kernels
+int fast_pass_table_size(int n);
+// fill the per-pass twiddle table (host doubles, interleaved re/im) from
+// tw[j] = exp(-2 pi i j / n) given as cos/sin pairs
+void fast_pass_table(int n, const double* tw_re_im, double* out_re_im);
 template <typename T, int N>
 cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st);
 template <typename T, int N>

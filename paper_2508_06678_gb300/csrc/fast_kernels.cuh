@@ -83,7 +83,7 @@ struct RowCtx {
   C* b0;
   C* b1;
   int ph;
-  typename E::Tw tw;
+  const C* tw;  // per-pass twiddle table
   const Geom* g;
   int bad;
 
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
   cx.b0 = sm + (size_t)(2 * lr) * E::BUF;
   cx.b1 = cx.b0 + E::BUF;
   cx.ph = 0;
-  cx.tw = E::load_tw(cx.t, tw);
+  cx.tw = tw;
   cx.g = &g;
   cx.bad = 0;
   if (d.flag) {
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   C* b0 = sm + c * CP;
   C* b1 = sm + (W + c) * CP;
   int ph = 0;
-  const typename E::Tw twb = E::load_tw(t, tw);
+  const C* twb = tw;
   if (d.flag) {
     if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
   }

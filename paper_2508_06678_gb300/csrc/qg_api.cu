@@ -114,6 +114,44 @@ void cos_sin_frac(long j, long n, double* c, double* s) {
 }  // namespace
 
 namespace qg {
+// Non-first passes of the specialised FFT in order (radix-16 passes, then the
+// last pass of radix 2^(log2 n mod 4)); each contributes (R - 1) * NS entries
+// [r - 1][k] = W_n^(r k n / (NS R)).
+static void for_each_pass(int n, void (*fn)(int, int, int, void*), void* ctx) {
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  const int np16 = lg / 4, rlast = 1 << (lg % 4);
+  int off = 0, ns = 16;
+  for (int p = 1; p < np16; ++p, ns *= 16) {
+    fn(16, ns, off, ctx);
+    off += 15 * ns;
+  }
+  if (rlast > 1) fn(rlast, n / rlast, off, ctx);
+}
+
+int fast_pass_table_size(int n) {
+  int total = 0;
+  for_each_pass(n, [](int R, int NS, int off, void* c) { *(int*)c = off + (R - 1) * NS; }, &total);
+  return total;
+}
+
+void fast_pass_table(int n, const double* tw, double* out) {
+  struct Ctx { int n; const double* tw; double* out; } cx{n, tw, out};
+  for_each_pass(
+      n,
+      [](int R, int NS, int off, void* c) {
+        Ctx& x = *(Ctx*)c;
+        for (int r = 1; r < R; ++r)
+          for (int k = 0; k < NS; ++k) {
+            const long j = ((long)r * k * (x.n / (NS * R))) % x.n;
+            const size_t e = (size_t)off + (size_t)(r - 1) * NS + k;
+            x.out[2 * e] = x.tw[2 * j];
+            x.out[2 * e + 1] = x.tw[2 * j + 1];
+          }
+      },
+      &cx);
+}
+
 // Lets other translation units of the library report through qg_last_error().
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace qg
@@ -149,6 +187,7 @@ struct qg_handle {
   void* fac_b = nullptr;
   void* fac_s = nullptr;
   void* tw = nullptr;
+  void* ptw = nullptr;  // per-pass twiddle table of the power-of-two kernels
   void* visc_x = nullptr;
   void* visc_y = nullptr;
   void* phys = nullptr;
@@ -242,11 +281,11 @@ struct Bracket {
 template <typename T>
 cudaError_t row_fast_dispatch(qg_handle* h, const RowDesc& d) {
   switch (h->g.n) {
-    case 256: return launch_row_fast<T, 256>(h->g, d, h->tw, h->stream);
-    case 512: return launch_row_fast<T, 512>(h->g, d, h->tw, h->stream);
-    case 1024: return launch_row_fast<T, 1024>(h->g, d, h->tw, h->stream);
-    case 2048: return launch_row_fast<T, 2048>(h->g, d, h->tw, h->stream);
-    case 4096: return launch_row_fast<T, 4096>(h->g, d, h->tw, h->stream);
+    case 256: return launch_row_fast<T, 256>(h->g, d, h->ptw, h->stream);
+    case 512: return launch_row_fast<T, 512>(h->g, d, h->ptw, h->stream);
+    case 1024: return launch_row_fast<T, 1024>(h->g, d, h->ptw, h->stream);
+    case 2048: return launch_row_fast<T, 2048>(h->g, d, h->ptw, h->stream);
+    case 4096: return launch_row_fast<T, 4096>(h->g, d, h->ptw, h->stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -254,11 +293,11 @@ cudaError_t row_fast_dispatch(qg_handle* h, const RowDesc& d) {
 template <typename T>
 cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
   switch (h->g.n) {
-    case 256: return launch_col_fast<T, 256>(h->g, d, h->tw, h->stream);
-    case 512: return launch_col_fast<T, 512>(h->g, d, h->tw, h->stream);
-    case 1024: return launch_col_fast<T, 1024>(h->g, d, h->tw, h->stream);
-    case 2048: return launch_col_fast<T, 2048>(h->g, d, h->tw, h->stream);
-    case 4096: return launch_col_fast<T, 4096>(h->g, d, h->tw, h->stream);
+    case 256: return launch_col_fast<T, 256>(h->g, d, h->ptw, h->stream);
+    case 512: return launch_col_fast<T, 512>(h->g, d, h->ptw, h->stream);
+    case 1024: return launch_col_fast<T, 1024>(h->g, d, h->ptw, h->stream);
+    case 2048: return launch_col_fast<T, 2048>(h->g, d, h->ptw, h->stream);
+    case 4096: return launch_col_fast<T, 4096>(h->g, d, h->ptw, h->stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -632,6 +671,15 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
       tw[2 * j + 1] = -s;
     }
     if ((rc = upload_real(h, h->tw, tw))) { delete h; return rc; }
+    if (h->fast) {
+      const int nt = fast_pass_table_size(n);
+      std::vector<double> pt(2 * (size_t)(nt > 0 ? nt : 1), 0.0);
+      fast_pass_table(n, tw.data(), pt.data());
+      if ((rc = dalloc(h, &h->ptw, pt.size() / 2 * csz)) || (rc = upload_real(h, h->ptw, pt))) {
+        delete h;
+        return rc;
+      }
+    }
   }
   // exact viscous factors, separable in k_x and k_y
   {

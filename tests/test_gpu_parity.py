@@ -278,3 +278,35 @@ def test_apriori_rejects_unsupported_sizes():
         qg.qg_sgs_apriori(w, 64, 2 * math.pi, None, None, qg_closure(1, 0, 0.2, 2.0),
                           qg_params(2e-3, 5e-3, 0.0, 1e-3, 50.0), 0.5, 5.0)
     assert ei.value.code == qg.QG_ERR_UNSUPPORTED
+
+
+def test_full_size_production_step_fp64():
+    """2048^2 dynamic Leith, FP64 form: two steps against the oracle."""
+    wl = S.island2048_dleith()
+    w0 = wl.omega0()
+    ref = O.QGOracle(wl.n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure), O.Params())
+    ref.set_state(w0)
+    ref.step(2)
+    with qg.QGSolver.from_workload(wl, precision=qg.QG_FP64) as s:
+        s.set_state(w0)
+        s.step(2)
+        got = s.get_state()
+    assert rel(got, ref.get_state()) < 1e-12
+
+
+def test_full_size_fp32_error_against_fp64_100_steps():
+    """The FP32 form's vorticity error against the (oracle-pinned) FP64 form at
+    2048^2 after 100 steps stays within 2e-4; energy and enstrophy within 0.5%."""
+    wl = S.island2048_dleith()
+    w0 = wl.omega0()
+    out = {}
+    for prec in (qg.QG_FP64, qg.QG_FP32):
+        with qg.QGSolver.from_workload(wl, precision=prec) as s:
+            s.set_state(w0)
+            s.step(100)
+            out[prec] = (s.get_state(), s.diagnostics())
+    err = rel(out[qg.QG_FP32][0], out[qg.QG_FP64][0])
+    assert err < 2e-4, err
+    for key in ("energy", "enstrophy"):
+        a, b = out[qg.QG_FP32][1][key], out[qg.QG_FP64][1][key]
+        assert abs(a - b) < 5e-3 * abs(b)
