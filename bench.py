@@ -48,6 +48,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of a per-rank float over the process group (identity without one).
+
+    Uses a CUDA tensor under NCCL and a CPU tensor under gloo.
+    """
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(n: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job grid-point-steps/s of `world` replicas, each advancing an n^2 grid `steps` steps."""
+    return world * n * n * steps / (ms_max / 1e3)
+
+
 def algorithmic_bytes(wl, precision_fp32: bool):
     """Minimal HBM bytes per launch of each kernel class of one step.
 
@@ -258,11 +278,8 @@ def main():
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     solver.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * wl.n * wl.n * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms)
+    value = replica_value(wl.n, args.steps, world, ms)
 
     # ---- per-kernel durations: a second pass of the same K steps with a CUDA
     # event pair recorded around every launch on the solver's stream (the
@@ -320,10 +337,7 @@ def main():
     diag = solver.diagnostics(raise_nonfinite=False)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s)
     esz = 4 if fp32 else 8
     e2e = {"value": world * wl.n * wl.n * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": wl.n * wl.n * esz / args.steps,

@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py: the replicas' max-over-ranks timing (gloo, 2 ranks on CPU)
+and the algorithmic byte model."""
+import os
+import socket
+
+import pytest
+
+import bench
+import synth as S
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 10.0 + 5.0 * rank  # the slower rank decides
+    m = bench.max_over_ranks(ms)
+    q.put((rank, m, bench.replica_value(2048, 100, world, m)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for _, m, v in res:
+        assert m == 15.0
+        assert v == pytest.approx(2 * 2048 * 2048 * 100 / 0.015)
+
+
+def test_max_over_ranks_without_group():
+    assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_algorithmic_byte_model_production():
+    m = bench.algorithmic_bytes(S.island2048_dleith(), True)
+    n, K = 2048, 682
+    I = n * (K + 1) * 8
+    assert m["row_stage"] == (3, 14 * I)
+    step = sum(a * b for a, b in m.values())
+    assert 1.2e9 < step < 1.3e9
