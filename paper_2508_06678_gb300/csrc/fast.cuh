@@ -169,7 +169,8 @@ int fast_pass_table_size(int n);
 void fast_pass_table(int n, const double* tw_re_im, double* out_re_im);
 template <typename T, int N>
 cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st);
+struct TmaSet;
 template <typename T, int N>
-cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cudaStream_t st);
+cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, const TmaSet& tm, cudaStream_t st);
 
 }  // namespace qg

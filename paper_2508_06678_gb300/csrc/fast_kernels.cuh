@@ -6,10 +6,8 @@
 
 #include "fast.cuh"
 #include "qg_kernels.h"
+#include "tma.cuh"
 
-#ifndef QG_PREFETCH
-#define QG_PREFETCH 1
-#endif
 #ifndef QG_ROW_MINB
 #define QG_ROW_MINB 4
 #endif
@@ -53,7 +51,17 @@ template <int N> struct ColCfg {
   static constexpr int THREADS = W * TT;
   // column stride in shared memory (complex elements): 16 / W mod 16 keeps the exchanges conflict-free
   static constexpr int CP = N + N / 16 + 16 / W;
+  static constexpr int BR = N < 256 ? N : 256;  // rows per TMA box
+  static constexpr int NBOX = N / BR;
 };
+// bytes of one shared-memory stage: a dense W x N tile for TMA, or W padded exchange columns
+template <typename T, int N> __host__ __device__ constexpr int col_stage_bytes() {
+  constexpr int dense = N * ColCfg<N>::W * 2 * (int)sizeof(T);
+  constexpr int padded = ColCfg<N>::W * ColCfg<N>::CP * 2 * (int)sizeof(T);
+  return ((dense > padded ? dense : padded) + 1023) / 1024 * 1024;
+}
+// bounded device waits: about one second of SM clocks
+constexpr long long kWaitCycles = 2000000000LL;
 
 template <typename T>
 __device__ __forceinline__ void leith_p(T u, T v, T wx, T wy, T& J, T& P, T& Q) {
@@ -298,8 +306,8 @@ template <> struct FInvK2<float> {
 };
 
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(Geom g, ColDesc d,
-                                                                       const cplx_t<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(
+    Geom g, ColDesc d, const cplx_t<T>* __restrict__ tw, const __grid_constant__ TmaSet tm) {
   using E = E16<T, N>;
   using C = cplx_t<T>;
   constexpr int W = ColCfg<N>::W;
@@ -307,20 +315,46 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   constexpr int CP = ColCfg<N>::CP;
   constexpr int K = E::K;
   constexpr int Ny = 2 * K + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BR = ColCfg<N>::BR;
+  constexpr int NBOX = ColCfg<N>::NBOX;
+  constexpr int SB = col_stage_bytes<T, N>();
+  constexpr uint32_t FIELD_BYTES = (uint32_t)N * W * 2 * sizeof(T);
+  // shared memory: exchange buffer | stage 0 | stage 1.  A stage receives a
+  // field's dense W x N tile by TMA, then serves as the FFT's second exchange
+  // buffer, and in the inverse phase holds the dense output tile for the TMA store.
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ double red[2][32];
-  C* sm = reinterpret_cast<C*>(smem_raw);
+  __shared__ __align__(8) uint64_t mbar[2];
+  // TMA tiles need 128-byte aligned shared addresses: align the base explicitly (1 KB slack is allocated)
+  unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  C* xbuf = reinterpret_cast<C*>(sbase);
+  C* stage[2] = {reinterpret_cast<C*>(sbase + SB), reinterpret_cast<C*>(sbase + 2 * SB)};
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
   const int mx = blockIdx.x * W + c;
+  const int c0 = blockIdx.x * W;
   const bool col_ok = mx < E::Kc;
-  C* b0 = sm + c * CP;
-  C* b1 = sm + (W + c) * CP;
+  const bool lead = threadIdx.x == 0;
   int ph = 0;
   const C* twb = tw;
   if (d.flag) {
     if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
   }
+  // thread 0 starts the first two forward fields' tiles
+  if (lead) {
+    tma::mbar_init(&mbar[0], 1);
+    tma::mbar_init(&mbar[1], 1);
+    tma::fence_mbar_init();
+    if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
+      for (int f = 0; f < d.nfwd && f < 2; ++f) {
+        tma::mbar_expect_tx(&mbar[f], FIELD_BYTES);
+        for (int bx = 0; bx < NBOX; ++bx)
+          tma::load_2d(reinterpret_cast<unsigned char*>(stage[f]) + (size_t)bx * BR * W * sizeof(C), &tm.in[f],
+                       2 * c0, bx * BR, &mbar[f]);
+      }
+    }
+  }
+  __syncthreads();
   const double ks2 = g.kscale * g.kscale;
   const double n2 = double(N) * double(N);
   const T kxv = T(g.kscale) * T(mx);
@@ -335,31 +369,33 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
 
   // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
   if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
-#if QG_PREFETCH
-    C xn[16];
-    {
-      const C* src = reinterpret_cast<const C*>(d.fin[0]) + mx;
-#pragma unroll
-      for (int m = 0; m < 16; ++m) xn[m] = src[(size_t)(t + TT * m) * g.IP];
-    }
-#endif
 #pragma unroll 1
     for (int f = 0; f < d.nfwd; ++f) {
-#if QG_PREFETCH
-      // field f arrived in xn; start loading field f + 1 before transforming f
-#pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = xn[m];
-      if (f + 1 < d.nfwd) {
-        const C* nsrc = reinterpret_cast<const C*>(d.fin[f + 1]) + mx;
-#pragma unroll
-        for (int m = 0; m < 16; ++m) xn[m] = nsrc[(size_t)(t + TT * m) * g.IP];
+      const int sidx = f & 1;
+      C* st = stage[sidx];
+      const bool ok = tma::mbar_wait(&mbar[sidx], (f >> 1) & 1, kWaitCycles);
+      if (__syncthreads_or(!ok)) {
+        // a tile never arrived: report, give the copy one more bounded wait, leave together
+        if (lead) {
+          if (d.err) atomicOr(d.err, kFlagTimeout);
+          tma::mbar_wait(&mbar[sidx], (f >> 1) & 1, kWaitCycles);
+        }
+        __syncthreads();
+        return;
       }
-#else
-      const C* src = reinterpret_cast<const C*>(d.fin[f]) + mx;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = src[(size_t)(t + TT * m) * g.IP];
-#endif
-      E::run(x, t, b0, b1, ph, twb, -1);
+      for (int m = 0; m < 16; ++m) x[m] = st[(t + TT * m) * W + c];
+      ph = 0;
+      E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, -1);
+      // every thread is done with this stage: hand it to the TMA for field f + 2
+      tma::fence_proxy_async();
+      __syncthreads();
+      if (lead && f + 2 < d.nfwd) {
+        tma::mbar_expect_tx(&mbar[sidx], FIELD_BYTES);
+        for (int bx = 0; bx < NBOX; ++bx)
+          tma::load_2d(reinterpret_cast<unsigned char*>(st) + (size_t)bx * BR * W * sizeof(C), &tm.in[f + 2],
+                       2 * c0, bx * BR, &mbar[sidx]);
+      }
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k = t + TT * m;
@@ -563,11 +599,25 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
           break;
       }
 #undef QG_KY
-      E::run(x, t, b0, b1, ph, twb, +1);
-      C* dst = reinterpret_cast<C*>(d.dout[q]) + mx;
+      C* st = stage[q & 1];
+      // the store issued from this stage two fields ago has finished reading it
+      if (lead) tma::wait_group_read<1>();
+      __syncthreads();
+      ph = 0;
+      E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, +1);
+      __syncthreads();  // all exchange reads of the stage are done
 #pragma unroll
-      for (int m = 0; m < 16; ++m) dst[(size_t)(t + TT * m) * g.IP] = x[m];
+      for (int m = 0; m < 16; ++m) st[(t + TT * m) * W + c] = x[m];
+      tma::fence_proxy_async();
+      __syncthreads();
+      if (lead) {
+        for (int bx = 0; bx < NBOX; ++bx)
+          tma::store_2d(&tm.out[q], 2 * c0, bx * BR,
+                        reinterpret_cast<const unsigned char*>(st) + (size_t)bx * BR * W * sizeof(C));
+        tma::commit_group();
+      }
     }
+    if (lead) tma::wait_group_all();
   }
 }
 
@@ -611,10 +661,9 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
 }
 
 template <typename T, int N>
-cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cudaStream_t st) {
-  using E = fast::E16<T, N>;
+cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, const TmaSet& tm, cudaStream_t st) {
   using Cfg = fast::ColCfg<N>;
-  const size_t smem = (size_t)2 * Cfg::W * Cfg::CP * sizeof(cplx_t<T>);
+  const size_t smem = (size_t)3 * fast::col_stage_bytes<T, N>() + 1024;
   const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);
   const int grid = g.Kcp / Cfg::W;
   cudaError_t e = cudaSuccess;
@@ -629,7 +678,7 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cud
       if (e != cudaSuccess) return e;                                                                    \
       if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
     }                                                                                                    \
-    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp);                                                     \
+    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp, tm);                                                 \
     break;                                                                                               \
   }
   switch (d.op) {
@@ -643,7 +692,6 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cud
       return cudaErrorInvalidValue;
   }
 #undef QG_COL_CASE
-  (void)E::BUF;
   return cudaGetLastError();
 }
 
@@ -651,7 +699,9 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, cud
   template <> int fast_col_width<N>() { return fast::ColCfg<N>::W; }                                    \
   template cudaError_t launch_row_fast<float, N>(const Geom&, const RowDesc&, const void*, cudaStream_t);  \
   template cudaError_t launch_row_fast<double, N>(const Geom&, const RowDesc&, const void*, cudaStream_t); \
-  template cudaError_t launch_col_fast<float, N>(const Geom&, const ColDesc&, const void*, cudaStream_t);  \
-  template cudaError_t launch_col_fast<double, N>(const Geom&, const ColDesc&, const void*, cudaStream_t);
+  template cudaError_t launch_col_fast<float, N>(const Geom&, const ColDesc&, const void*, const TmaSet&,       \
+                                                 cudaStream_t);                                             \
+  template cudaError_t launch_col_fast<double, N>(const Geom&, const ColDesc&, const void*, const TmaSet&,      \
+                                                  cudaStream_t);
 
 }  // namespace qg

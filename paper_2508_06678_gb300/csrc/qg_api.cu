@@ -23,9 +23,12 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/qg.h"
 #include "fast.cuh"
 #include "qg_kernels.h"
+#include "tma.cuh"
 
 using namespace qg;
 
@@ -202,6 +205,8 @@ struct qg_handle {
   int64_t step = 0;
   double t = 0;
   std::vector<void*> allocs;
+  // TMA tensor maps of the mixed arrays (power-of-two kernels)
+  std::vector<std::pair<const void*, CUtensorMap>> maps;
   // tracing
   bool prof = false;
   int32_t launches[QG_NUM_KCLASS] = {};
@@ -228,6 +233,42 @@ int dalloc(qg_handle* h, void** p, size_t bytes) {
   e = cudaMemsetAsync(*p, 0, bytes, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   return QG_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D map of one mixed array [y][k_x] (complex, IP columns, n rows); a box is
+// W columns (2W reals, 16 or 32 bytes) by BR rows
+int add_tensor_map(qg_handle* h, const void* base, int W, int BR) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(QG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * h->g.IP, (cuuint64_t)h->g.n};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * h->g.IP * h->esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * W), (cuuint32_t)BR};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(&m, h->fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(QG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  h->maps.push_back({base, m});
+  return QG_OK;
+}
+
+const CUtensorMap* find_map(const qg_handle* h, const void* base) {
+  for (const auto& e : h->maps)
+    if (e.first == base) return &e.second;
+  return nullptr;
 }
 
 // upload host doubles as the handle's working precision
@@ -292,12 +333,24 @@ cudaError_t row_fast_dispatch(qg_handle* h, const RowDesc& d) {
 
 template <typename T>
 cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
+  TmaSet tm;
+  memset(&tm, 0, sizeof(tm));
+  for (int f = 0; f < d.nfwd; ++f) {
+    const CUtensorMap* m = find_map(h, d.fin[f]);
+    if (!m) return cudaErrorInvalidValue;
+    tm.in[f] = *m;
+  }
+  for (int q = 0; q < d.nder; ++q) {
+    const CUtensorMap* m = find_map(h, d.dout[q]);
+    if (!m) return cudaErrorInvalidValue;
+    tm.out[q] = *m;
+  }
   switch (h->g.n) {
-    case 256: return launch_col_fast<T, 256>(h->g, d, h->ptw, h->stream);
-    case 512: return launch_col_fast<T, 512>(h->g, d, h->ptw, h->stream);
-    case 1024: return launch_col_fast<T, 1024>(h->g, d, h->ptw, h->stream);
-    case 2048: return launch_col_fast<T, 2048>(h->g, d, h->ptw, h->stream);
-    case 4096: return launch_col_fast<T, 4096>(h->g, d, h->ptw, h->stream);
+    case 256: return launch_col_fast<T, 256>(h->g, d, h->ptw, tm, h->stream);
+    case 512: return launch_col_fast<T, 512>(h->g, d, h->ptw, tm, h->stream);
+    case 1024: return launch_col_fast<T, 1024>(h->g, d, h->ptw, tm, h->stream);
+    case 2048: return launch_col_fast<T, 2048>(h->g, d, h->ptw, tm, h->stream);
+    case 4096: return launch_col_fast<T, 4096>(h->g, d, h->ptw, tm, h->stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -318,6 +371,7 @@ int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
 
 int run_col(qg_handle* h, ColDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
+  d.err = h->flag;
   Bracket br(h, cls);
   cudaError_t e;
   if (h->fast)
@@ -618,7 +672,8 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
       case 2048: fw = fast_col_width<2048>(); break;
       case 4096: fw = fast_col_width<4096>(); break;
     }
-    const size_t fast_col_smem = (size_t)2 * fw * (n + n / 16 + 16 / fw) * csz;
+    const size_t dense = (size_t)n * fw * csz, padded = (size_t)fw * (n + n / 16 + 16 / fw) * csz;
+    const size_t fast_col_smem = 3 * (((dense > padded ? dense : padded) + 1023) / 1024 * 1024) + 1024;
     const size_t fast_row_smem = (size_t)2 * (n >= 2048 ? 1 : 2048 / n) * (n + n / 16) * csz;
     h->fast = pow2 && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
     if (getenv("QG_FORCE_GENERIC")) h->fast = false;
@@ -680,6 +735,14 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
         return rc;
       }
     }
+  }
+  // tensor maps of every mixed array for the TMA column pass
+  if (h->fast) {
+    const int BR = n < 256 ? n : 256;
+    for (int i = 0; i < kMaxIn; ++i)
+      if (h->X[i] && (rc = add_tensor_map(h, h->X[i], h->W, BR))) { delete h; return rc; }
+    for (int i = 0; i < kMaxOut; ++i)
+      if (h->Y[i] && (rc = add_tensor_map(h, h->Y[i], h->W, BR))) { delete h; return rc; }
   }
   // exact viscous factors, separable in k_x and k_y
   {
@@ -812,6 +875,7 @@ int qg_sync(qg_handle* h) {
   CK(cudaStreamSynchronize(h->stream), "qg_sync");
   h->flag_pending = false;
   f = *h->flag_host;
+  if (f & kFlagTimeout) return fail(QG_ERR_TIMEOUT, "qg_sync: a bounded device wait gave up (TMA tile never arrived)");
   if (f) return fail(QG_ERR_NONFINITE, "qg_sync: state became non-finite");
   return QG_OK;
 }

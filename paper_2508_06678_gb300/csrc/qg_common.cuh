@@ -148,7 +148,8 @@ struct ColDesc {
   const void* visc_x;  // exp(-nu kx^2 dt), per m_x
   const void* visc_y;  // exp(-nu ky^2 dt), per r
   double visc_mu;      // exp(-mu dt)
-  int* flag;
+  int* flag;           // stop flag checked at entry (NULL: always run)
+  int* err;            // status bits raised by bounded waits that give up (NULL: not reported)
 };
 
 // Per-thread accumulator of the Germano sums.  FP64 fields accumulate in
