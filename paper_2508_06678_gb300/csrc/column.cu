@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
       }
       if (d.viscous) wn = cscale(wn, vx[mx] * vy[r] * vmu);
       if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
-      if (d.store_ws) ws[gi] = wn;
+      if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
       if (d.store_w0) w0[gi] = wn;
     }
     slotA[e] = wn;

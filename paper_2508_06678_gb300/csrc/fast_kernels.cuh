@@ -15,7 +15,7 @@
 #define QG_COL_MINB 2
 #endif
 #ifndef QG_COL_MINB_REDUCE
-#define QG_COL_MINB_REDUCE 1
+#define QG_COL_MINB_REDUCE 2
 #endif
 #ifndef QG_COL_MINB_FWD
 #define QG_COL_MINB_FWD 1
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
         }
         if (d.viscous) wn = cscale(wn, vx[mx] * vy[r] * vmu);
         if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
-        if (d.store_ws) ws[gi] = wn;
+        if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
         if (d.store_w0) w0[gi] = wn;
       }
       A[m] = wn;

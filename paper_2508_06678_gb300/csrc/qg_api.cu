@@ -183,6 +183,7 @@ struct qg_handle {
   // device buffers
   void* w0 = nullptr;
   void* ws = nullptr;
+  void* ws2 = nullptr;  // second stage-state array (stages alternate between ws and ws2)
   void* jh = nullptr;
   void* dh = nullptr;
   void* X[kMaxIn] = {};
@@ -388,6 +389,7 @@ ColDesc col_base(qg_handle* h) {
   ColDesc d{};
   d.w0 = h->w0;
   d.ws = h->ws;
+  d.ws_out = h->ws;
   d.jh = h->jh;
   d.dh = h->dh;
   d.dt = h->par.dt;
@@ -406,6 +408,7 @@ ColDesc col_base(qg_handle* h) {
   d.visc_mu = h->visc_mu;
   return d;
 }
+
 
 void set_stage_derived(qg_handle* h, ColDesc& d) {
   d.nder = h->nder;
@@ -458,6 +461,8 @@ int enqueue_step(qg_handle* h) {
     c.a = kRK[s][0];
     c.b = kRK[s][1];
     c.use_ws = s > 0;
+    c.ws = s == 2 ? h->ws2 : h->ws;      // stage 1 state in ws, stage 2 state in ws2
+    c.ws_out = s == 0 ? h->ws : h->ws2;
     if (h->dynamic) {
       ColDesc cr = c;
       cr.op = CO_DYN_REDUCE;
@@ -689,6 +694,7 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   const size_t phys_bytes = (size_t)n * n * h->esz;
   if (!rc) rc = dalloc(h, &h->w0, spec_bytes);
   if (!rc) rc = dalloc(h, &h->ws, spec_bytes);
+  if (!rc) rc = dalloc(h, &h->ws2, spec_bytes);
   if (!rc && h->dynamic) rc = dalloc(h, &h->jh, spec_bytes);
   if (!rc && h->dynamic) rc = dalloc(h, &h->dh, spec_bytes);
   for (int i = 0; i < h->nin && !rc; ++i) rc = dalloc(h, &h->X[i], mixed_bytes);

@@ -126,7 +126,8 @@ struct ColDesc {
   void* dout[kMaxDer];
   // spectral arrays
   void* w0;        // state w^n (read; written when store_w0)
-  void* ws;        // RK stage state (read when use_ws; written when store_ws)
+  void* ws;        // RK stage state read when use_ws
+  void* ws_out;    // RK stage state written when store_ws (a different array, so split passes never race)
   void* jh;        // dynamic closures: stored J_hat
   void* dh;        // dynamic closures: stored D_hat
   int use_ws;      // the stage input is ws (else w0)
