@@ -208,6 +208,12 @@ struct qg_handle {
   std::vector<void*> allocs;
   // TMA tensor maps of the mixed arrays (power-of-two kernels)
   std::vector<std::pair<const void*, CUtensorMap>> maps;
+  // one step captured as a CUDA graph and replayed by qg_step (eager launches
+  // while tracing, or where the stream cannot be captured)
+  cudaGraphExec_t step_graph = nullptr;
+  bool graph_tried = false;
+  int64_t eager_steps = 0;
+  int32_t graph_launches[QG_NUM_KCLASS] = {};
   // tracing
   bool prof = false;
   int32_t launches[QG_NUM_KCLASS] = {};
@@ -217,6 +223,7 @@ struct qg_handle {
   std::vector<cudaEvent_t> pool;
 
   ~qg_handle() {
+    if (step_graph) cudaGraphExecDestroy(step_graph);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -530,6 +537,37 @@ int enqueue_step(qg_handle* h) {
   h->step += 1;
   h->t += h->par.dt;
   return QG_OK;
+}
+
+// Capture one step on the handle's stream into a graph.  Needs a capturable
+// (non-legacy) stream and one eager step first (kernel attributes set).
+void try_build_graph(qg_handle* h) {
+  h->graph_tried = true;
+  if (!h->stream || getenv("QG_NO_GRAPH")) return;
+  int32_t saved[QG_NUM_KCLASS];
+  memcpy(saved, h->launches, sizeof(saved));
+  const int64_t step = h->step;
+  const double t = h->t;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int rc = enqueue_step(h);
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  for (int i = 0; i < QG_NUM_KCLASS; ++i) h->graph_launches[i] = h->launches[i] - saved[i];
+  memcpy(h->launches, saved, sizeof(saved));
+  h->step = step;
+  h->t = t;
+  if (rc != QG_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) h->step_graph = ex;
+  cudaGraphDestroy(g);
+  cudaGetLastError();
 }
 
 // physical field of the state into h->phys (working precision)
@@ -863,8 +901,17 @@ int qg_step(qg_handle* h, int32_t nsteps) {
   if (!h->flag_pending && *h->flag_host)
     return fail(QG_ERR_NONFINITE, "qg_step: state became non-finite at an earlier step");
   for (int i = 0; i < nsteps; ++i) {
-    int rc = enqueue_step(h);
-    if (rc) return rc;
+    if (!h->prof && h->eager_steps > 0 && !h->graph_tried) try_build_graph(h);
+    if (!h->prof && h->step_graph) {
+      CK(cudaGraphLaunch(h->step_graph, h->stream), "qg_step: graph launch");
+      for (int c = 0; c < QG_NUM_KCLASS; ++c) h->launches[c] += h->graph_launches[c];
+      h->step += 1;
+      h->t += h->par.dt;
+    } else {
+      int rc = enqueue_step(h);
+      if (rc) return rc;
+      h->eager_steps += 1;
+    }
   }
   if (!h->flag_pending) {
     CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "qg_step: flag");

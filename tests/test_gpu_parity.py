@@ -310,3 +310,26 @@ def test_full_size_fp32_error_against_fp64_100_steps():
     for key in ("energy", "enstrophy"):
         a, b = out[qg.QG_FP32][1][key], out[qg.QG_FP64][1][key]
         assert abs(a - b) < 5e-3 * abs(b)
+
+
+@pytest.mark.parametrize("n,prec", [(256, qg.QG_FP32), (96, qg.QG_FP64), (2048, qg.QG_FP32)])
+def test_graph_replay_is_bitwise_eager(n, prec, monkeypatch):
+    """qg_step replays one captured step as a CUDA graph on a capturable stream;
+    the result is bit-identical to launching the same kernels one by one."""
+    import torch
+    wl = S.Workload("t", n, "island", beta=5.0, U=0.5, closure=S.DLEITH, radius=0.5, seed=2)
+    w0 = S.init_field(2, n, k_peak=n / 8)
+    out = []
+    for eager in (False, True):
+        if eager:
+            monkeypatch.setenv("QG_NO_GRAPH", "1")
+        else:
+            monkeypatch.delenv("QG_NO_GRAPH", raising=False)
+        stream = torch.cuda.Stream()
+        with qg.QGSolver.from_workload(wl, precision=prec, stream=stream) as s:
+            s.set_state(w0)
+            s.step(1)
+            s.step(7)
+            out.append((s.get_state(), s.diagnostics()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["step"] == out[1][1]["step"] == 8
