@@ -68,6 +68,7 @@ __all__ = [
     "obstacle_forcing_hat", "sponge_forcing_hat",
     "rk3_step", "viscous_substep", "brinkman_substep", "sponge_substep", "full_step",
     "energy", "enstrophy", "sgs_apriori", "pcc", "apriori_filter",
+    "AB2CN", "RK3_EXACT", "AB2History", "ab2cn_step",
 ]
 
 NONE, SMAG, LEITH, DSMAG, DLEITH = 0, 1, 2, 3, 4
@@ -80,6 +81,9 @@ class Closure:
     test_ratio: float = 2.0
 
 
+RK3_EXACT, AB2CN = 0, 1
+
+
 @dataclass
 class Params:
     dt: float = 2e-3
@@ -87,6 +91,7 @@ class Params:
     mu: float = 0.0
     eta: float = 1e-3
     sponge_rate: float = 50.0
+    scheme: int = RK3_EXACT
 
 
 class Ops:
@@ -280,6 +285,49 @@ def full_step(ops: Ops, wh: np.ndarray, beta: float, U: float, closure: Closure,
     return w, coeffs
 
 
+@dataclass
+class AB2History:
+    """History of the paper's scheme: the explicit terms at the previous step and
+    the previous step's intermediate field w** (Sec. II-E, Eq. 4)."""
+    E: np.ndarray
+    w_star: np.ndarray
+
+
+def ab2cn_step(ops: Ops, wh: np.ndarray, hist, beta: float, U: float, closure: Closure, params: Params,
+               chi, chi_s):
+    """One step of the paper's scheme (Sec. II-E, Eq. 4).
+
+    w*   = w^t + dt/2 (nu lap - mu - beta d/dx)(w* + w^t) + dt (3/2 E^t - 1/2 E^{t-1})
+           with the explicit terms E = -J(psi, w) + C div(g grad w) - curl(chi u / eta)
+           (Crank-Nicolson on the linear terms, AB2 on the Jacobian, the closure and
+           the Brinkman forcing; the closure term joins the explicit part in LES);
+    w^{t+1} = w* - dt rate chi_s (3/2 w* - 1/2 w**), w** the previous step's w*,
+           then the 2/3 truncation and the mean mode set to zero.
+    The first step (no history) takes E^{t-1} = E^t and w** = w* (Euler start).
+    Returns (w^{t+1}, new history, C).
+    """
+    dt = params.dt
+    E = -jacobian_hat(ops, wh, U)
+    C = 0.0
+    if closure.kind != NONE:
+        C = closure_coefficient(ops, wh, closure, U)
+        E = E + C * sgs_divergence_hat(ops, wh, closure.kind)
+    if chi is not None:
+        u, v = velocity(ops, wh, U)
+        E = E - ops.T * (1j * ops.kx * ops.fwd(chi * v) - 1j * ops.ky * ops.fwd(chi * u)) / params.eta
+    E_prev = E if hist is None else hist.E
+    lin = -(params.nu * ops.k2 + params.mu) + 1j * beta * ops.kx * ops.inv_k2
+    w_star = ((1.0 + 0.5 * dt * lin) * wh + dt * (1.5 * E - 0.5 * E_prev)) / (1.0 - 0.5 * dt * lin)
+    w_new = w_star
+    if chi_s is not None:
+        w_ss = w_star if hist is None else hist.w_star
+        Z = ops.inv(1.5 * w_star - 0.5 * w_ss)
+        w_new = w_star - ops.T * ops.fwd(dt * params.sponge_rate * chi_s * Z)
+    w_new = ops.T * w_new
+    w_new[0, 0] = 0.0
+    return w_new, AB2History(E, w_star), C
+
+
 def energy(ops: Ops, wh: np.ndarray) -> float:
     """E = <|u'|^2> / 2 of the perturbation velocity (no inflow), physical mean."""
     u, v = velocity(ops, wh, 0.0)
@@ -302,20 +350,28 @@ class QGOracle:
         self.chi_s = None if sponge is None else np.asarray(sponge, dtype=np.float64).reshape(n, n)
         self.closure, self.params = closure, params
         self.wh = np.zeros((n, n // 2 + 1), dtype=np.complex128)
+        self.hist = None
         self.t = 0.0
         self.step_count = 0
         self.last_coeff = 0.0
 
     def set_state(self, omega):
         self.wh = project(self.ops, omega)
+        self.hist = None
 
     def get_state(self) -> np.ndarray:
         return to_physical(self.ops, self.wh)
 
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
-            self.wh, coeffs = full_step(self.ops, self.wh, self.beta, self.U, self.closure, self.params, self.chi, self.chi_s)
-            self.last_coeff = coeffs[-1]
+            if self.params.scheme == AB2CN:
+                self.wh, self.hist, C = ab2cn_step(self.ops, self.wh, self.hist, self.beta, self.U, self.closure,
+                                                   self.params, self.chi, self.chi_s)
+                self.last_coeff = C
+            else:
+                self.wh, coeffs = full_step(self.ops, self.wh, self.beta, self.U, self.closure, self.params, self.chi,
+                                            self.chi_s)
+                self.last_coeff = coeffs[-1]
             self.step_count += 1
             self.t += self.params.dt
 
