@@ -78,11 +78,23 @@ typedef struct {
   double test_ratio;
 } qg_closure;
 
+/* Time schemes.  QG_SCHEME_RK3_EXACT (default): SSP-RK3 for J, beta and the
+ * SGS term, then exact viscous, Brinkman and sponge sub-steps.
+ * QG_SCHEME_AB2CN: the paper's own scheme (Sec. II-E, Eq. 4): Crank-Nicolson on
+ * nu lap - mu - beta d/dx, AB2 on the Jacobian, the SGS term and the Brinkman
+ * forcing, then the sponge split advanced by AB2 with the w*, w** history;
+ * the first step after qg_set_state is an Euler start.  AB2CN treats the
+ * penalisation explicitly, so it needs eta > dt (Sec. II-E). */
+#define QG_SCHEME_RK3_EXACT 0
+#define QG_SCHEME_AB2CN 1
+
 /* Time-step parameters: dt, viscosity nu = 1/Re, bottom friction mu,
- * porosity eta of the Brinkman term (Eq. 2) and sponge rate = 1/eta_sponge
- * (Eq. 3). */
+ * porosity eta of the Brinkman term (Eq. 2), sponge rate = 1/eta_sponge
+ * (Eq. 3) and the time scheme. */
 typedef struct {
   double dt, nu, mu, eta, sponge_rate;
+  int32_t scheme;
+  int32_t reserved;
 } qg_params;
 
 /* Diagnostics of the current state.  energy = <|u'|^2>/2 of the perturbation

@@ -20,6 +20,8 @@ QG_ERR_TIMEOUT = -5
 QG_ERR_UNSUPPORTED = -6
 QG_FP64 = 0
 QG_FP32 = 1
+QG_SCHEME_RK3_EXACT = 0
+QG_SCHEME_AB2CN = 1
 QG_NONE, QG_SMAG, QG_LEITH, QG_DSMAG, QG_DLEITH = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("row_stage", "col_reduce", "col_stage", "row_brinkman", "col_curl", "row_sponge", "col_final",
                   "other")
@@ -40,7 +42,7 @@ class qg_closure(C.Structure):
 
 class qg_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("nu", C.c_double), ("mu", C.c_double), ("eta", C.c_double),
-                ("sponge_rate", C.c_double)]
+                ("sponge_rate", C.c_double), ("scheme", C.c_int32), ("reserved", C.c_int32)]
 
 
 class qg_diag(C.Structure):

@@ -126,6 +126,12 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
             slotA[e] = in_test ? csub(X, slotA[e]) : X;
           } else if (f == 4) {                                       // M = r^p D~ - G D
             slotB[e] = cadd(slotB[e], cscale(X, rpow));
+          } else if (f == 6) {  // Brinkman pair of the paper's scheme: F_obs = (i ky F[chi u] - i kx F[chi v]) / eta
+            slotA[e] = cscale(cmul_ik(X, ky), T(d.inv_eta));
+          } else if (f == 7) {
+            const T kx = T(g.kscale) * T(mx);
+            slotA[e] = csub(slotA[e], cscale(cmul_ik(X, kx), T(d.inv_eta)));
+            reinterpret_cast<C*>(d.bh)[gi] = slotA[e];
           } else {
             const C M = cadd(slotB[e], cscale(cmul_ik(X, ky), rpow));
             const C H = slotA[e];
@@ -146,6 +152,14 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
             slotA[e] = csub(cmul_ik(X, kx), cmul_ik(slotA[e], ky));  // i kx v - i ky u
           }
           break;
+        case CO_AB2CN: {  // E = -J + C D + F_obs: slot A collects -J + F_obs, slot B collects D
+          const T kx = T(g.kscale) * T(mx);
+          if (f == 0) slotA[e] = mk<C>(-X.x, -X.y);
+          else if (f < d.nst) slotB[e] = (f == 1) ? X : cadd(slotB[e], cmul_ik(X, ky));
+          else if (f == d.nst) slotA[e] = cadd(slotA[e], cscale(cmul_ik(X, ky), T(d.inv_eta)));
+          else slotA[e] = csub(slotA[e], cscale(cmul_ik(X, kx), T(d.inv_eta)));
+          break;
+        }
         default:  // CO_FORWARD
           slotA[e] = X;
           break;
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
 
   // ---- coefficient of the dynamic closures from the partial sums (same order in every CTA)
   T coeff = T(d.coeff);
-  if (d.op == CO_DYN_COMBINE) {
+  if (d.op == CO_DYN_COMBINE || d.op == CO_AB2CN_COMBINE) {
     if (tid < 32) {
       double a = 0.0, b = 0.0;
       for (int i = tid; i < d.npartials; i += 32) {
@@ -243,6 +257,46 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
           break;
         }
+        case CO_AB2CN:
+        case CO_AB2CN_COMBINE: {
+          // Eq. 4: w* = ((1 + dt/2 lin) w^t + dt (3/2 E - 1/2 E_prev)) / (1 - dt/2 lin)
+          C E;
+          if (d.op == CO_AB2CN) {
+            E = (d.nst > 1) ? cadd(slotA[e], cscale(slotB[e], coeff)) : slotA[e];
+          } else {
+            const C J = jh[gi];
+            E = cadd(mk<C>(-J.x, -J.y), cscale(dh[gi], coeff));
+            if (d.brink) E = cadd(E, reinterpret_cast<const C*>(d.bh)[gi]);
+          }
+          C* ep = reinterpret_cast<C*>(d.eprev);
+          const C Ep = d.ab2_first ? E : ep[gi];
+          ep[gi] = E;
+          const int m2 = mx * mx + my * my;
+          const T k2 = T(ks2) * T(m2);
+          const T ik2 = InvK2<T>::get(ks2, m2);
+          const T kx = T(g.kscale) * T(mx);
+          const T hdt = T(0.5) * dt;
+          const T lre = -(T(d.nu) * k2 + T(d.mu));
+          const T lim = beta * kx * ik2;
+          const C wz = w0[gi];
+          const C ab = mk<C>(T(1.5) * E.x - T(0.5) * Ep.x, T(1.5) * E.y - T(0.5) * Ep.y);
+          const C num = cadd(cmul(mk<C>(T(1) + hdt * lre, hdt * lim), wz), cscale(ab, dt));
+          const T dre = T(1) - hdt * lre, dim = -hdt * lim;
+          const T den = dre * dre + dim * dim;
+          const C wst = mk<C>((num.x * dre + num.y * dim) / den, (num.y * dre - num.x * dim) / den);
+          if (d.sponge_next) {
+            C* wsp = reinterpret_cast<C*>(d.wss);
+            const C wss = d.ab2_first ? wst : wsp[gi];
+            wsp[gi] = wst;
+            wn = mk<C>(T(1.5) * wst.x - T(0.5) * wss.x, T(1.5) * wst.y - T(0.5) * wss.y);
+          } else {
+            wn = wst;
+          }
+          break;
+        }
+        case CO_AB2CN_FINAL:
+          wn = csub(reinterpret_cast<const C*>(d.wss)[gi], slotA[e]);
+          break;
         default:  // CO_CURL, CO_FORWARD
           wn = slotA[e];
           break;

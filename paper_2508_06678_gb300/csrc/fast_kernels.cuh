@@ -36,7 +36,7 @@ template <int N> struct RowCfg {
 template <typename T, int OP = -1> struct Occ {
   static constexpr int row = QG_ROW_MINB;
   static constexpr int col = OP == CO_DYN_REDUCE ? QG_COL_MINB_REDUCE
-                             : OP == CO_FORWARD ? QG_COL_MINB_FWD
+                             : (OP == CO_FORWARD || OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
                              : OP == CO_CURL    ? QG_COL_MINB_CURL
                                                 : QG_COL_MINB;
 };
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
     tma::mbar_init(&mbar[0], 1);
     tma::mbar_init(&mbar[1], 1);
     tma::fence_mbar_init();
-    if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
+    if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE && OP != CO_AB2CN_COMBINE) {
       for (int f = 0; f < d.nfwd && f < 2; ++f) {
         tma::mbar_expect_tx(&mbar[f], FIELD_BYTES);
         for (int bx = 0; bx < NBOX; ++bx)
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   GermanoAcc<T> acc_hm, acc_mm;
 
   // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
-  if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE) {
+  if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE && OP != CO_AB2CN_COMBINE) {
 #pragma unroll 1
     for (int f = 0; f < d.nfwd; ++f) {
       const int sidx = f & 1;
@@ -423,6 +423,11 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
             A[m] = in_test ? csub(X, A[m]) : X;
           } else if (f == 4) {
             B[m] = cadd(B[m], cscale(X, T(d.rpow)));
+          } else if (f == 6) {  // Brinkman pair (paper's scheme): F_obs = (i ky F[chi u] - i kx F[chi v]) / eta
+            A[m] = cscale(cmul_ik(X, ky), T(d.inv_eta));
+          } else if (f == 7) {
+            A[m] = csub(A[m], cscale(cmul_ik(X, kxv), T(d.inv_eta)));
+            if (kept) reinterpret_cast<C*>(d.bh)[colbase + r] = A[m];
           } else {
             const C M = cadd(B[m], cscale(cmul_ik(X, ky), T(d.rpow)));
             const C H = A[m];
@@ -438,7 +443,13 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
         } else if constexpr (OP == CO_CURL) {
           if (f == 0) A[m] = X;
           else A[m] = csub(cmul_ik(X, kxv), cmul_ik(A[m], ky));
-        } else {  // CO_FORWARD
+        } else if constexpr (OP == CO_AB2CN) {
+          // E = -J + C D + F_obs: A collects -J + F_obs, B collects D
+          if (f == 0) A[m] = mk<C>(-X.x, -X.y);
+          else if (f < d.nst) B[m] = (f == 1) ? X : cadd(B[m], cmul_ik(X, ky));
+          else if (f == d.nst) A[m] = cadd(A[m], cscale(cmul_ik(X, ky), T(d.inv_eta)));
+          else A[m] = csub(A[m], cscale(cmul_ik(X, kxv), T(d.inv_eta)));
+        } else {  // CO_FORWARD, CO_AB2CN_FINAL
           A[m] = X;
         }
       }
@@ -473,7 +484,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
     return;
   } else {
     T coeff = T(d.coeff);
-    if constexpr (OP == CO_DYN_COMBINE) {
+    if constexpr (OP == CO_DYN_COMBINE || OP == CO_AB2CN_COMBINE) {
       if (threadIdx.x < 32) {
         double a = 0.0, b = 0.0;
         for (int i = threadIdx.x; i < d.npartials; i += 32) {
@@ -527,6 +538,42 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
           }
           const C inner = cadd(wst, cscale(L, dt));
           wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
+        } else if constexpr (OP == CO_AB2CN || OP == CO_AB2CN_COMBINE) {
+          // Eq. 4: w* = ((1 + dt/2 lin) w^t + dt (3/2 E - 1/2 E_prev)) / (1 - dt/2 lin)
+          C E;
+          if constexpr (OP == CO_AB2CN) {
+            E = (d.nst > 1) ? cadd(A[m], cscale(B[m], coeff)) : A[m];
+          } else {
+            const C J = jh[gi];
+            E = cadd(mk<C>(-J.x, -J.y), cscale(dh[gi], coeff));
+            if (d.brink) E = cadd(E, reinterpret_cast<const C*>(d.bh)[gi]);
+          }
+          C* ep = reinterpret_cast<C*>(d.eprev);
+          const C Ep = d.ab2_first ? E : ep[gi];
+          ep[gi] = E;
+          const int m2 = mx * mx + my * my;
+          const T k2 = T(ks2) * T(m2);
+          const T ik2 = FInvK2<T>::get(ks2, m2);
+          const T hdt = T(0.5) * dt;
+          const T lre = -(T(d.nu) * k2 + T(d.mu));
+          const T lim = beta * kxv * ik2;
+          const C wz = w0[gi];
+          const C ab = mk<C>(T(1.5) * E.x - T(0.5) * Ep.x, T(1.5) * E.y - T(0.5) * Ep.y);
+          const C num = cadd(cmul(mk<C>(T(1) + hdt * lre, hdt * lim), wz), cscale(ab, dt));
+          const T dre = T(1) - hdt * lre, dim = -hdt * lim;
+          const T den = dre * dre + dim * dim;
+          const C wst = mk<C>((num.x * dre + num.y * dim) / den, (num.y * dre - num.x * dim) / den);
+          if (d.sponge_next) {
+            C* wsp = reinterpret_cast<C*>(d.wss);
+            const C wss = d.ab2_first ? wst : wsp[gi];
+            wsp[gi] = wst;
+            wn = mk<C>(T(1.5) * wst.x - T(0.5) * wss.x, T(1.5) * wst.y - T(0.5) * wss.y);
+          } else {
+            wn = wst;
+          }
+        } else if constexpr (OP == CO_AB2CN_FINAL) {
+          const C wst = reinterpret_cast<const C*>(d.wss)[gi];
+          wn = csub(wst, A[m]);
         } else {
           wn = A[m];
         }
@@ -688,6 +735,9 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, con
     QG_COL_CASE(CO_DYN_COMBINE)
     QG_COL_CASE(CO_CURL)
     QG_COL_CASE(CO_FORWARD)
+    QG_COL_CASE(CO_AB2CN)
+    QG_COL_CASE(CO_AB2CN_COMBINE)
+    QG_COL_CASE(CO_AB2CN_FINAL)
     default:
       return cudaErrorInvalidValue;
   }

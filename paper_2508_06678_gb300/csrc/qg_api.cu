@@ -187,7 +187,13 @@ struct qg_handle {
   void* jh = nullptr;
   void* dh = nullptr;
   void* X[kMaxIn] = {};
-  void* Y[kMaxOut] = {};
+  void* Y[kMaxY] = {};
+  // the paper's scheme (Eq. 4): history of the explicit terms and of w*, stored F_obs
+  int scheme = QG_SCHEME_RK3_EXACT;
+  void* eprev = nullptr;
+  void* wss = nullptr;
+  void* bh = nullptr;
+  bool ab2_hist = false;
   void* fac_b = nullptr;
   void* fac_s = nullptr;
   void* tw = nullptr;
@@ -413,6 +419,13 @@ ColDesc col_base(qg_handle* h) {
   d.visc_x = h->visc_x;
   d.visc_y = h->visc_y;
   d.visc_mu = h->visc_mu;
+  d.eprev = h->eprev;
+  d.wss = h->wss;
+  d.bh = h->bh;
+  d.ab2_first = h->ab2_hist ? 0 : 1;
+  d.inv_eta = h->par.eta > 0 ? 1.0 / h->par.eta : 0.0;
+  d.nu = h->par.nu;
+  d.mu = h->par.mu;
   return d;
 }
 
@@ -539,6 +552,8 @@ int enqueue_step(qg_handle* h) {
   return QG_OK;
 }
 
+int enqueue_any_step(qg_handle* h);
+
 // Capture one step on the handle's stream into a graph.  Needs a capturable
 // (non-legacy) stream and one eager step first (kernel attributes set).
 void try_build_graph(qg_handle* h) {
@@ -553,8 +568,10 @@ void try_build_graph(qg_handle* h) {
     cudaGetLastError();
     return;
   }
-  const int rc = enqueue_step(h);
+  const bool hist = h->ab2_hist;
+  const int rc = enqueue_any_step(h);
   const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  h->ab2_hist = hist;
   for (int i = 0; i < QG_NUM_KCLASS; ++i) h->graph_launches[i] = h->launches[i] - saved[i];
   memcpy(h->launches, saved, sizeof(saved));
   h->step = step;
@@ -569,6 +586,90 @@ void try_build_graph(qg_handle* h) {
   cudaGraphDestroy(g);
   cudaGetLastError();
 }
+
+// One step of the paper's scheme (Sec. II-E, Eq. 4):
+//   row pass     products of the closure (as an RK stage) [+ chi (u_total, v)]
+//   column pass  E = -J + C D + F_obs, w* by Crank-Nicolson / AB2; then either
+//                Z = 3/2 w* - 1/2 w** for the sponge or the next state
+//   sponge       row pass s = dt rate chi_s Z; column pass w^{t+1} = w* - s
+int enqueue_step_ab2(qg_handle* h) {
+  int rc;
+  RowDesc r{};
+  r.prog = h->row_prog;
+  r.nin = h->nin;
+  r.nout = h->nout;
+  r.dx_mask = h->dx_mask;
+  r.check_finite = 1;
+  for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
+  for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
+  if ((rc = run_row(h, r, QG_K_ROW_STAGE))) return rc;
+  if (h->fac_b) {  // chi (u_total, v): X[0], X[1] hold the stage's u_total and v
+    RowDesc b{};
+    b.prog = RP_SCALE;
+    b.nin = b.nout = 2;
+    b.in[0] = h->X[0];
+    b.in[1] = h->X[1];
+    b.out[0] = h->Y[6];
+    b.out[1] = h->Y[7];
+    b.factor = h->fac_b;
+    b.check_finite = 1;
+    if ((rc = run_row(h, b, QG_K_ROW_BRINK))) return rc;
+  }
+  ColDesc c = col_base(h);
+  c.brink = h->fac_b ? 1 : 0;
+  if (h->dynamic) {
+    ColDesc cr = c;
+    cr.op = CO_DYN_REDUCE;
+    cr.nfwd = h->fac_b ? 8 : 6;
+    for (int i = 0; i < 6; ++i) cr.fin[i] = h->Y[i];
+    cr.fin[6] = h->Y[6];
+    cr.fin[7] = h->Y[7];
+    if ((rc = run_col(h, cr, QG_K_COL_REDUCE))) return rc;
+    c.op = CO_AB2CN_COMBINE;
+    c.nfwd = 0;
+    c.coeff_out = h->dev_scalars + 2;
+  } else {
+    c.op = CO_AB2CN;
+    c.nst = h->nout;
+    c.nfwd = h->nout + (h->fac_b ? 2 : 0);
+    for (int i = 0; i < h->nout; ++i) c.fin[i] = h->Y[i];
+    if (h->fac_b) {
+      c.fin[h->nout] = h->Y[6];
+      c.fin[h->nout + 1] = h->Y[7];
+    }
+  }
+  if (h->fac_s) {
+    c.sponge_next = 1;
+    c.nder = 1;
+    c.der[0] = D_W;
+    c.dout[0] = h->X[0];
+  } else {
+    set_final(h, c);
+  }
+  if ((rc = run_col(h, c, h->fac_s ? QG_K_COL_STAGE : QG_K_COL_FINAL))) return rc;
+  if (h->fac_s) {
+    RowDesc sp{};
+    sp.prog = RP_SCALE;
+    sp.nin = sp.nout = 1;
+    sp.in[0] = h->X[0];
+    sp.out[0] = h->Y[0];
+    sp.factor = h->fac_s;
+    sp.check_finite = 1;
+    if ((rc = run_row(h, sp, QG_K_ROW_SPONGE))) return rc;
+    ColDesc f = col_base(h);
+    f.op = CO_AB2CN_FINAL;
+    f.nfwd = 1;
+    f.fin[0] = h->Y[0];
+    set_final(h, f);
+    if ((rc = run_col(h, f, QG_K_COL_FINAL))) return rc;
+  }
+  h->ab2_hist = true;
+  h->step += 1;
+  h->t += h->par.dt;
+  return QG_OK;
+}
+
+int enqueue_any_step(qg_handle* h) { return h->scheme == QG_SCHEME_AB2CN ? enqueue_step_ab2(h) : enqueue_step(h); }
 
 // physical field of the state into h->phys (working precision)
 int state_to_phys(qg_handle* h) {
@@ -612,6 +713,8 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   if (!(params->dt > 0) || params->nu < 0 || params->mu < 0 || (mask && !(params->eta > 0)) ||
       (sponge && params->sponge_rate < 0))
     return fail(QG_ERR_ARG, "qg_create: bad time-step parameters");
+  if (params->scheme != QG_SCHEME_RK3_EXACT && params->scheme != QG_SCHEME_AB2CN)
+    return fail(QG_ERR_ARG, "qg_create: unknown time scheme %d", params->scheme);
 
   qg_handle* h = new qg_handle();
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -622,6 +725,7 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   h->U = U;
   h->cl = *closure;
   h->par = *params;
+  h->scheme = params->scheme;
   h->dynamic = closure->kind == QG_DSMAG || closure->kind == QG_DLEITH;
   const double delta = grid->L / n;
   {
@@ -738,6 +842,13 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   for (int i = 0; i < h->nin && !rc; ++i) rc = dalloc(h, &h->X[i], mixed_bytes);
   const int ny = h->nout > 2 ? h->nout : 2;
   for (int i = 0; i < ny && !rc; ++i) rc = dalloc(h, &h->Y[i], mixed_bytes);
+  if (h->scheme == QG_SCHEME_AB2CN) {
+    if (!rc && mask) rc = dalloc(h, &h->Y[6], mixed_bytes);
+    if (!rc && mask) rc = dalloc(h, &h->Y[7], mixed_bytes);
+    if (!rc) rc = dalloc(h, &h->eprev, spec_bytes);
+    if (!rc) rc = dalloc(h, &h->wss, spec_bytes);
+    if (!rc && mask && h->dynamic) rc = dalloc(h, &h->bh, spec_bytes);
+  }
   if (!rc) rc = dalloc(h, &h->phys, phys_bytes);
   if (!rc) rc = dalloc(h, &h->tw, (size_t)n * csz);
   if (!rc) rc = dalloc(h, &h->visc_x, (size_t)g.Kcp * h->esz);
@@ -785,7 +896,7 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     const int BR = n < 256 ? n : 256;
     for (int i = 0; i < kMaxIn; ++i)
       if (h->X[i] && (rc = add_tensor_map(h, h->X[i], h->W, BR))) { delete h; return rc; }
-    for (int i = 0; i < kMaxOut; ++i)
+    for (int i = 0; i < kMaxY; ++i)
       if (h->Y[i] && (rc = add_tensor_map(h, h->Y[i], h->W, BR))) { delete h; return rc; }
   }
   // exact viscous factors, separable in k_x and k_y
@@ -804,14 +915,18 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     if ((rc = upload_real(h, h->visc_x, vx)) || (rc = upload_real(h, h->visc_y, vy))) { delete h; return rc; }
   }
   // exact penalisation factors
+  // RK3 + exact sub-steps: exp(-chi dt / eta) and exp(-rate chi_s dt);
+  // the paper's scheme: chi itself (explicit Brinkman forcing) and dt rate chi_s (AB2 sponge)
+  const bool ab2 = h->scheme == QG_SCHEME_AB2CN;
   if (mask) {
     std::vector<double> f((size_t)n * n);
-    for (size_t i = 0; i < f.size(); ++i) f[i] = std::exp(-mask[i] * params->dt / params->eta);
+    for (size_t i = 0; i < f.size(); ++i) f[i] = ab2 ? mask[i] : std::exp(-mask[i] * params->dt / params->eta);
     if ((rc = upload_real(h, h->fac_b, f))) { delete h; return rc; }
   }
   if (sponge) {
     std::vector<double> f((size_t)n * n);
-    for (size_t i = 0; i < f.size(); ++i) f[i] = std::exp(-params->sponge_rate * sponge[i] * params->dt);
+    for (size_t i = 0; i < f.size(); ++i)
+      f[i] = ab2 ? params->dt * params->sponge_rate * sponge[i] : std::exp(-params->sponge_rate * sponge[i] * params->dt);
     if ((rc = upload_real(h, h->fac_s, f))) { delete h; return rc; }
   }
   // the zero state derives to zero fields: X already zeroed
@@ -849,6 +964,7 @@ int qg_set_state(qg_handle* h, const void* omega, int32_t on_device, int32_t dty
   }
   CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "qg_set_state: flag");
   h->flag_pending = false;
+  h->ab2_hist = false;
   *h->flag_host = 0;
   RowDesc r{};
   r.prog = RP_COPY;
@@ -901,14 +1017,16 @@ int qg_step(qg_handle* h, int32_t nsteps) {
   if (!h->flag_pending && *h->flag_host)
     return fail(QG_ERR_NONFINITE, "qg_step: state became non-finite at an earlier step");
   for (int i = 0; i < nsteps; ++i) {
-    if (!h->prof && h->eager_steps > 0 && !h->graph_tried) try_build_graph(h);
-    if (!h->prof && h->step_graph) {
+    // the Euler start of the paper's scheme differs from its later steps: always eager
+    const bool start = h->scheme == QG_SCHEME_AB2CN && !h->ab2_hist;
+    if (!h->prof && !start && h->eager_steps > 0 && !h->graph_tried) try_build_graph(h);
+    if (!h->prof && !start && h->step_graph) {
       CK(cudaGraphLaunch(h->step_graph, h->stream), "qg_step: graph launch");
       for (int c = 0; c < QG_NUM_KCLASS; ++c) h->launches[c] += h->graph_launches[c];
       h->step += 1;
       h->t += h->par.dt;
     } else {
-      int rc = enqueue_step(h);
+      int rc = enqueue_any_step(h);
       if (rc) return rc;
       h->eager_steps += 1;
     }

@@ -65,7 +65,8 @@ __host__ __device__ __forceinline__ int row_of_r(const Geom& g, int r) { return 
 constexpr int kMaxIn = 12;   // max fields entering one row pass
 constexpr int kMaxOut = 6;   // max fields leaving one row pass
 constexpr int kMaxDer = 12;  // max derived fields leaving one column pass
-constexpr int kMaxFwd = 6;   // max fields entering one column pass
+constexpr int kMaxFwd = 8;   // max fields entering one column pass
+constexpr int kMaxY = 8;     // row-pass output arrays of a handle
 
 // Codes of the spectral fields a column pass derives from a vorticity
 // spectrum w (all scaled by 1/N^2 so that the two inverse passes return
@@ -100,6 +101,10 @@ enum ColOp : int {
   CO_DYN_COMBINE = 3,  // L = -J - beta v + C D with C from the partial sums; RK combine
   CO_CURL = 4,         // forward u, v; w = i kx v - i ky u
   CO_FORWARD = 5,      // forward one field; w = that field
+  // the paper's scheme (Eq. 4)
+  CO_AB2CN = 6,          // forward J[, P, Q][, chi u, chi v]; CN / AB2 combine; sponge field or next state
+  CO_AB2CN_COMBINE = 7,  // as CO_AB2CN from stored J, D, F_obs and the Germano partial sums
+  CO_AB2CN_FINAL = 8,    // forward s = dt rate chi_s Z; w^{t+1} = w* - s
 };
 
 struct RowDesc {
@@ -146,6 +151,15 @@ struct ColDesc {
   double* partials;
   int npartials;
   double* coeff_out;  // CO_DYN_COMBINE: block 0 writes C here
+  // the paper's scheme (Eq. 4)
+  void* bh;          // dynamic closures: stored Brinkman forcing F_obs (CO_DYN_REDUCE fields 6, 7)
+  void* eprev;       // explicit terms E of the previous step (read, then overwritten with this step's)
+  void* wss;         // w** (read) / w* (written) of the sponge split
+  int ab2_first;     // Euler start: E_prev = E, w** = w*
+  int nst;           // forward fields of the closure products before the Brinkman pair
+  int brink;         // the Brinkman pair chi u, chi v follows
+  int sponge_next;   // derive Z = 3/2 w* - 1/2 w** for the sponge (else the next state)
+  double inv_eta, nu, mu;
   const void* visc_x;  // exp(-nu kx^2 dt), per m_x
   const void* visc_y;  // exp(-nu ky^2 dt), per r
   double visc_mu;      // exp(-mu dt)

@@ -150,17 +150,17 @@ class QGSolver:
     def __init__(self, n: int, *, L: float = 2 * math.pi, precision: int = QG_FP64, beta: float = 0.0,
                  U: float = 0.0, mask=None, sponge=None, kind: int = 0, c: float = 0.0, test_ratio: float = 2.0,
                  dt: float = 2e-3, nu: float = 1.0 / 200.0, mu: float = 0.0, eta: float = 1e-3,
-                 sponge_rate: float = 50.0, stream=None):
+                 sponge_rate: float = 50.0, scheme: int = 0, stream=None):
         self.cfg = _Cfg(n, L, precision)
         self.h = 0
         self.h = qg_create(qg_grid(n, precision, L), beta, U, mask, sponge, qg_closure(kind, 0, c, test_ratio),
-                           qg_params(dt, nu, mu, eta, sponge_rate), stream)
+                           qg_params(dt, nu, mu, eta, sponge_rate, scheme, 0), stream)
 
     @classmethod
-    def from_workload(cls, wl, precision: int = QG_FP64, stream=None) -> "QGSolver":
+    def from_workload(cls, wl, precision: int = QG_FP64, stream=None, scheme: int = 0) -> "QGSolver":
         return cls(wl.n, L=wl.L, precision=precision, beta=wl.beta, U=wl.U, mask=wl.mask(),
                    sponge=wl.sponge_field(), kind=wl.closure, c=wl.c, test_ratio=wl.test_ratio, dt=wl.dt,
-                   nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, stream=stream)
+                   nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, scheme=scheme, stream=stream)
 
     def set_state(self, omega) -> None:
         qg_set_state(self.h, omega, self.cfg.n)

@@ -49,7 +49,7 @@ def test_struct_layouts_match_header(lib):
     from paper_2508_06678_gb300._lib import qg_closure, qg_diag, qg_grid, qg_params
     assert C.sizeof(qg_grid) == 16
     assert C.sizeof(qg_closure) == 24
-    assert C.sizeof(qg_params) == 40
+    assert C.sizeof(qg_params) == 48
     assert C.sizeof(qg_diag) == 56
 
 

@@ -333,3 +333,75 @@ def test_graph_replay_is_bitwise_eager(n, prec, monkeypatch):
             out.append((s.get_state(), s.diagnostics()))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1]["step"] == out[1][1]["step"] == 8
+
+
+# --------------------------------------------------------------------------
+# The paper's own scheme (Sec. II-E, Eq. 4): CN / AB2 with the AB2 sponge split
+# --------------------------------------------------------------------------
+
+def make_ab2_pair(n, kind, precision=qg.QG_FP64, seed=1, k_peak=None, geometry="island", beta=5.0, U=0.5,
+                  stream=None):
+    dt, eta = 5e-4, 2e-3  # the scheme treats the penalisation explicitly: eta > dt (Sec. II-E)
+    wl = S.Workload("t", n, geometry, beta=beta, U=U, closure=kind, c=0.2, radius=0.8, seed=seed, dt=dt, eta=eta)
+    w0 = S.init_field(seed, n, k_peak=k_peak or max(4.0, n / 8))
+    mask = wl.mask()
+    sp = wl.sponge_field()
+    ref = O.QGOracle(n, wl.L, beta, U, mask, sp, O.Closure(kind, c=0.2),
+                     O.Params(dt=dt, eta=eta, scheme=O.AB2CN))
+    ref.set_state(w0)
+    gpu = qg.QGSolver(n, L=wl.L, precision=precision, beta=beta, U=U, mask=mask, sponge=sp, kind=kind, c=0.2,
+                      dt=dt, eta=eta, scheme=qg.QG_SCHEME_AB2CN, stream=stream)
+    gpu.set_state(w0)
+    return ref, gpu, w0
+
+
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+@pytest.mark.parametrize("n", [48, 54, 256])
+def test_ab2cn_parity_fp64(kind, n):
+    ref, gpu, _ = make_ab2_pair(n, kind, k_peak=n / 6)
+    for steps in (1, 59):
+        ref.step(steps)
+        gpu.step(steps)
+        err = rel(gpu.get_state(), ref.get_state())
+        assert err < 1e-11, (steps, err)
+    if kind in (S.DSMAG, S.DLEITH):
+        assert gpu.diagnostics()["coeff"] == pytest.approx(ref.last_coeff, rel=1e-9, abs=1e-300)
+    gpu.close()
+
+
+@pytest.mark.parametrize("kind", [S.SMAG, S.DLEITH])
+def test_ab2cn_parity_fp32_cape(kind):
+    ref, gpu, _ = make_ab2_pair(256, kind, precision=qg.QG_FP32, geometry="cape", beta=10.0, U=1.0, seed=2)
+    ref.step(100)
+    gpu.step(100)
+    assert rel(gpu.get_state(), ref.get_state()) < 2e-4
+    gpu.close()
+
+
+def test_ab2cn_history_restarts_after_set_state():
+    ref, gpu, w0 = make_ab2_pair(48, S.LEITH)
+    ref.step(5)
+    gpu.step(5)
+    w_mid = S.init_field(9, 48, k_peak=8.0)
+    ref.set_state(w_mid)
+    gpu.set_state(w_mid)
+    ref.step(7)
+    gpu.step(7)
+    assert rel(gpu.get_state(), ref.get_state()) < 1e-12
+    gpu.close()
+
+
+def test_ab2cn_graph_replay_is_bitwise_eager(monkeypatch):
+    import torch
+    out = []
+    for eager in (False, True):
+        if eager:
+            monkeypatch.setenv("QG_NO_GRAPH", "1")
+        else:
+            monkeypatch.delenv("QG_NO_GRAPH", raising=False)
+        _, gpu, _ = make_ab2_pair(256, S.DSMAG, precision=qg.QG_FP32, stream=torch.cuda.Stream())
+        gpu.step(1)
+        gpu.step(9)
+        out.append(gpu.get_state())
+        gpu.close()
+    assert np.array_equal(out[0], out[1])
