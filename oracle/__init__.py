@@ -7,6 +7,8 @@ CUDA path; both receive their inputs from ``synth``.
 
 Every function cites the part of the paper (section / equation) it follows.
 Where the paper is silent or garbled the reading taken is documented beside
-the function.  Parity status per function is stated in ``qg.__doc__``.
+the function.  Parity status per function is stated in ``qg.__doc__`` and
+``apost.__doc__``.
 """
 from .qg import *  # noqa: F401,F403
+from .apost import *  # noqa: F401,F403

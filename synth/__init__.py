@@ -200,3 +200,33 @@ def cape512(closure: int, seed: int = 1) -> Workload:
 def island2048_dleith() -> Workload:
     """Production step past an island at 2048^2 with the dynamic Leith closure."""
     return Workload("island2048-dleith", 2048, "island", beta=5.0, U=0.5, closure=DLEITH, radius=0.2, seed=0, steps=5000)
+
+
+def wave_series(seed: int, n: int, nsnap: int, L: float = 2 * math.pi, speed=(0.5, 0.25), t0: float = 0.0,
+                dt_snap: float = 1.0, nmodes: int = 6, noise: float = 0.0, noise_seed: int | None = None) -> np.ndarray:
+    """A seeded snapshot series of a pattern translating at a uniform speed.
+
+    Snapshot i is f(x - c_x t_i, y - c_y t_i) + noise, t_i = t0 + i dt_snap,
+    where f = sum of ``nmodes`` cosines with integer wavevectors |m| <= 6,
+    amplitudes in [0.5, 1.5) and phases in [0, 2 pi), all drawn from
+    SplitMix64(seed).  ``noise`` adds white noise of that standard deviation
+    (stream ``noise_seed``, default seed + 1).  Evaluated pointwise (no
+    transforms).  Returns float64 of shape (nsnap, n, n).
+    """
+    u = uniform01(seed, 4 * nmodes)
+    mx = np.floor(u[0::4] * 13).astype(int) - 6
+    my = np.floor(u[1::4] * 13).astype(int) - 6
+    mx[(mx == 0) & (my == 0)] = 1
+    amp = 0.5 + u[2::4]
+    phase = 2 * math.pi * u[3::4]
+    x, y, _ = _coords(n, L)
+    k0 = 2 * math.pi / L
+    out = np.zeros((nsnap, n, n))
+    for i in range(nsnap):
+        t = t0 + i * dt_snap
+        xs, ys = x - speed[0] * t, y - speed[1] * t
+        for j in range(nmodes):
+            out[i] += amp[j] * np.cos(k0 * (mx[j] * xs + my[j] * ys) + phase[j])
+    if noise > 0:
+        out += noise * normal(seed + 1 if noise_seed is None else noise_seed, out.size).reshape(out.shape)
+    return out
