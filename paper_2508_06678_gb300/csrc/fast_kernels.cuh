@@ -603,9 +603,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
       A[m] = cscale(A[m], scale);
     }
     const T ksc = T(g.kscale);
+    int used = 0;  // fields transformed so far (alternates the two stages)
 #pragma unroll 1
     for (int q = 0; q < d.nder; ++q) {
       const int code = d.der[q];
+      // test-filtered fields vanish for k_x beyond the test band: their arrays stay zero there
+      if ((code & D_TEST) && c0 > d.test_kmax) continue;
       const unsigned on = (code & D_TEST) ? (keep & intest) : keep;
       C w[16];
 #pragma unroll
@@ -646,7 +649,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
           break;
       }
 #undef QG_KY
-      C* st = stage[q & 1];
+      C* st = stage[used & 1];
+      ++used;
       // the store issued from this stage two fields ago has finished reading it
       if (lead) tma::wait_group_read<1>();
       __syncthreads();

@@ -175,6 +175,7 @@ struct qg_handle {
   bool dynamic = false;
   double static_coeff = 0.0;
   int test_m2max = 0;  // largest |m|^2 the test filter keeps
+  int test_kmax = 0;   // largest k_x the test filter keeps
   // stage program
   int row_prog = RP_NONE, nin = 4, nout = 1;
   unsigned dx_mask = 0;
@@ -411,6 +412,7 @@ ColDesc col_base(qg_handle* h) {
   d.coeff = h->static_coeff;
   d.test_ratio = h->cl.test_ratio;
   d.test_m2max = h->test_m2max;
+  d.test_kmax = h->test_kmax;
   const int p = (h->cl.kind == QG_SMAG || h->cl.kind == QG_DSMAG) ? 2 : 3;
   d.closure_pow = p;
   d.rpow = std::pow(h->cl.test_ratio, p);
@@ -735,6 +737,9 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     int m2 = 0;
     while (m2 + 1 <= 2 * kmax * kmax && double(m2 + 1) * r2 <= double(n) * double(n)) ++m2;
     h->test_m2max = m2;
+    int kx = 0;
+    while ((kx + 1) * (kx + 1) <= m2) ++kx;
+    h->test_kmax = kx;
   }
   if (closure->kind == QG_SMAG) h->static_coeff = std::pow(closure->c * delta, 2);
   if (closure->kind == QG_LEITH) h->static_coeff = std::pow(closure->c * delta, 3);

@@ -146,6 +146,8 @@ struct ColDesc {
   int closure_pow;  // p of r^p in the Germano M
   double test_ratio;
   int test_m2max;   // test filter keeps |m|^2 <= test_m2max (exact integer form of |m| <= N / (2 r))
+  int test_kmax;    // largest k_x the test filter keeps; test-level fields vanish beyond it, and the
+                    // column pass leaves those columns of their mixed arrays at the zeros set at creation
   double rpow;      // r^p
   // Germano partial sums: written by CO_DYN_REDUCE (2 doubles per block), read by CO_DYN_COMBINE
   double* partials;
