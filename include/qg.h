@@ -168,6 +168,48 @@ int qg_sgs_apriori(const double* omega_fr, int32_t n_fr, int32_t n_les, double L
                    const double* sponge_fr, const qg_closure* closure, const qg_params* params, double U,
                    double beta, int32_t flags, double* pi_exact, double* pi_model, double* pi_parts, double* pcc);
 
+/* The grid filter of Eq. 5 alone, applied to a series of fully resolved
+ * fields: the filtered field omega_FF that an LES state is compared with a
+ * posteriori (Sec. IV).
+ *   omega_fr: nsnap >= 1 fields of n_fr*n_fr host doubles, row-major [y][x],
+ *             each projected onto its 2/3 band with zero mean first.
+ *   n_fr, n_les: grid sizes as for qg_sgs_apriori (n_les/2 - 1 must not exceed
+ *             the fine band (n_fr - 1)/3: QG_ERR_UNSUPPORTED otherwise).
+ *   flags: bit 0 set = omit the Gaussian factor.
+ *   omega_les: nsnap fields of n_les*n_les host doubles (output).
+ * Filter exp(-k^2 Delta^2 / 6) times the cut-off |k| <= pi/Delta, Delta =
+ * L/n_les, spectral copy to the coarse grid, coarse 2/3 band kept.  FP64 on
+ * the current device; synchronous; allocates its scratch per call. */
+int qg_grid_filter(const double* omega_fr, int32_t nsnap, int32_t n_fr, int32_t n_les, double L, int32_t flags,
+                   double* omega_les);
+
+/* A posteriori comparison of two snapshot series on one grid (Sec. IV,
+ * Eq. 15 and 16).
+ *   les: n_les_snap fields, ff: n_ff_snap fields (1 .. 2^20 each), npts >= 1
+ *        values per field, snapshot-major and contiguous; dtype QG_FP32 or
+ *        QG_FP64 for both; on_device = 1: device pointers (borrowed, read
+ *        only, used on stream), 0: host pointers (copied to the device).
+ *   lag_min <= lag_max: lags phi in snapshot intervals (at most 2^16 lags,
+ *        n_ff_snap * nlag <= 2^24); the pair (t, phi) compares les[t - phi]
+ *        with ff[t].
+ *   stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Outputs, host doubles, row t = ff snapshot, column j = phi - lag_min:
+ *   dist[n_ff_snap * nlag]: sum over the points of (les[t-phi] - ff[t])^2;
+ *   pcc[n_ff_snap * nlag] or NULL: PCC(les[t-phi], ff[t]) of Eq. 15 with
+ *        population moments, NaN where either field is constant;
+ *   entries whose t - phi lies outside [0, n_les_snap) are NaN in both;
+ *   mean_dist[nlag] or NULL: the mean of each column of dist over its
+ *        defined entries (NaN if none);
+ *   phase or NULL: the lag of Eq. 16, the phi of the smallest mean_dist
+ *        (ties: the smallest |phi|, then the negative lag).
+ * QG_ERR_ARG if no lag in the range pairs two snapshots.  FP32 series are
+ * differenced and multiplied in FP32 with each thread's sums compensated,
+ * chunk sums and all means in FP64; FP64 series run in FP64.  Deterministic;
+ * synchronous; allocates its scratch per call. */
+int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32_t n_ff_snap, int64_t npts,
+                      int32_t dtype, int32_t on_device, int32_t lag_min, int32_t lag_max, void* stream, double* dist,
+                      double* pcc, double* mean_dist, int32_t* phase);
+
 /* Kernel classes reported by qg_kernel_times. */
 #define QG_K_ROW_STAGE 0   /* row pass of an RK stage (products of Eq. 1, 9-14) */
 #define QG_K_COL_REDUCE 1  /* column pass: Germano partial sums (Eq. 12, 14) */

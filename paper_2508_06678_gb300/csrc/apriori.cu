@@ -575,3 +575,94 @@ extern "C" int qg_sgs_apriori(const double* omega_fr, int32_t n_fr, int32_t n_le
   }
   return QG_OK;
 }
+
+// The grid filter of Eq. 5 alone, on a series of fields: project each fine
+// field onto its 2/3 band (zero mean), filter and copy it to the coarse grid
+// (the coarse 2/3 band), return the physical coarse field.  This is the
+// filtered fully resolved field an LES is compared with a posteriori.
+extern "C" int qg_grid_filter(const double* omega_fr, int32_t nsnap, int32_t n_fr, int32_t n_les, double L,
+                              int32_t flags, double* omega_les) {
+  char msg[256];
+  if (!omega_fr || !omega_les) {
+    qg::set_last_error("qg_grid_filter: NULL argument");
+    return QG_ERR_ARG;
+  }
+  if (nsnap < 1 || !valid_n(n_fr) || !valid_n(n_les) || n_les > n_fr || !(L > 0)) {
+    snprintf(msg, sizeof(msg), "qg_grid_filter: bad sizes nsnap=%d n_fr=%d n_les=%d", nsnap, n_fr, n_les);
+    qg::set_last_error(msg);
+    return QG_ERR_ARG;
+  }
+  const int Kf = (n_fr - 1) / 3;
+  if (n_les / 2 - 1 > Kf) {
+    snprintf(msg, sizeof(msg),
+             "qg_grid_filter: the coarse band (n_les/2 - 1 = %d) exceeds the fine 2/3 band (%d); needs n_les <= %d",
+             n_les / 2 - 1, Kf, 2 * Kf + 2);
+    qg::set_last_error(msg);
+    return QG_ERR_UNSUPPORTED;
+  }
+  Grid F, Cg;
+  make_grid(F, n_fr, Kf, L, 2);
+  make_grid(Cg, n_les, (n_les - 1) / 3, L, 2);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (F.col_smem > (size_t)optin - 1024 || F.row_smem > (size_t)optin - 1024) {
+    qg::set_last_error("qg_grid_filter: grid too large for the kernels' shared memory");
+    return QG_ERR_UNSUPPORTED;
+  }
+  Pool pool;
+  Ctx cx;
+  for (Grid* G : {&F, &Cg}) {
+    std::vector<double> tw(2 * (size_t)G->g.n);
+    for (int j = 0; j < G->g.n; ++j) {
+      double c, s;
+      cos_sin_frac(j, G->g.n, &c, &s);
+      tw[2 * j] = c;
+      tw[2 * j + 1] = -s;
+    }
+    G->tw = pool.get(tw.size() * 8);
+    if (G->tw) cudaMemcpy(G->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
+  }
+  const size_t nf2 = (size_t)n_fr * n_fr, nc2 = (size_t)n_les * n_les;
+  void* Pw = pool.get(nf2 * 8);
+  void* Mf = pool.get((size_t)F.g.n * F.g.IP * 16);
+  void* Sw = pool.get((size_t)F.g.Kcp * F.g.SP * 16);
+  void* Mc = pool.get((size_t)Cg.g.n * Cg.g.IP * 16);
+  void* Cw = pool.get((size_t)Cg.g.Kcp * Cg.g.SP * 16);
+  void* Pc = pool.get(nc2 * 8);
+  if (pool.err != cudaSuccess) {
+    qg::set_last_error("qg_grid_filter: device allocation failed");
+    return QG_ERR_OOM;
+  }
+  qg_closure none{};
+  none.test_ratio = 2.0;
+  const ColDesc base = col_desc(0.0, &none, 0);
+  const double sc = (double(n_les) / double(n_fr)) * (double(n_les) / double(n_fr));
+  const int gauss = (flags & 1) ? 0 : 1;
+  for (int k = 0; k < nsnap && cx.err == cudaSuccess; ++k) {
+    cx.err = cudaMemcpy(Pw, omega_fr + (size_t)k * nf2, nf2 * 8, cudaMemcpyHostToDevice);
+    RowDesc r{};
+    r.prog = RP_COPY; r.nin = 1; r.nout = 1; r.in_phys = 1; r.phys_in = Pw; r.out[0] = Mf;
+    cx.row(F, r);
+    ColDesc c = base;
+    c.op = CO_FORWARD; c.nfwd = 1; c.fin[0] = Mf; c.w0 = Sw; c.store_w0 = 1; c.zero_mean = 1;
+    cx.col(F, c);
+    if (cx.err == cudaSuccess) {
+      filter_copy_kernel<<<256, 256, 0, cx.st>>>(F.g, (const C2*)Sw, Cg.g, (C2*)Cw, n_les, L / n_les, gauss, sc);
+      cx.err = cudaGetLastError();
+    }
+    ColDesc c2 = base;
+    c2.op = CO_DERIVE; c2.w0 = Cw; c2.nder = 1; c2.der[0] = D_W; c2.dout[0] = Mc;
+    cx.col(Cg, c2);
+    RowDesc r2{};
+    r2.prog = RP_COPY; r2.nin = 1; r2.nout = 1; r2.in[0] = Mc; r2.out_phys = 1; r2.phys_out = Pc;
+    cx.row(Cg, r2);
+    if (cx.err == cudaSuccess) cx.err = cudaMemcpy(omega_les + (size_t)k * nc2, Pc, nc2 * 8, cudaMemcpyDeviceToHost);
+  }
+  if (cx.err != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "qg_grid_filter: %s", cudaGetErrorString(cx.err));
+    qg::set_last_error(msg);
+    return QG_ERR_CUDA;
+  }
+  return QG_OK;
+}

@@ -16,7 +16,7 @@ from ._lib import (QG_ERR_NONFINITE, QG_FP32, QG_FP64, QG_OK, QGError, check, lo
                    qg_params)
 
 __all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_step", "qg_sync", "qg_diagnostics", "qg_destroy",
-           "qg_sgs_apriori", "qg_last_error", "qg_version", "QGSolver"]
+           "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_last_error", "qg_version", "QGSolver"]
 
 
 def _dptr(a):
@@ -135,6 +135,64 @@ def qg_sgs_apriori(omega_fr, n_les: int, L: float, mask_fr, sponge_fr, closure: 
                                pe.ctypes.data_as(P), pm.ctypes.data_as(P), parts.ctypes.data_as(P), C.byref(r))
     check(rc, "qg_sgs_apriori")
     return pe, pm, parts, r.value
+
+
+def qg_grid_filter(omega_fr, n_les: int, L: float, gaussian: bool = True):
+    """Grid filter of Eq. 5 on one fine field (n, n) or a series (nsnap, n, n); FP64 numpy out."""
+    w = np.ascontiguousarray(omega_fr, dtype=np.float64)
+    single = w.ndim == 2
+    if single:
+        w = w[None]
+    if w.ndim != 3 or w.shape[1] != w.shape[2]:
+        raise ValueError("omega_fr must be (n, n) or (nsnap, n, n)")
+    out = np.empty((w.shape[0], n_les, n_les))
+    P = C.POINTER(C.c_double)
+    rc = load().qg_grid_filter(w.ctypes.data_as(P), w.shape[0], w.shape[1], int(n_les), float(L),
+                               0 if gaussian else 1, out.ctypes.data_as(P))
+    check(rc, "qg_grid_filter")
+    return out[0] if single else out
+
+
+def _series(a):
+    """(pointer, nsnap, npts, dtype, on_device, keepalive) of a snapshot series."""
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        import torch
+        if not a.is_contiguous():
+            raise ValueError("device series must be contiguous")
+        if a.dtype not in (torch.float32, torch.float64):
+            raise TypeError("device series must be float32 or float64")
+        nsnap = a.shape[0]
+        return a.data_ptr(), nsnap, a.numel() // max(nsnap, 1), (QG_FP32 if a.dtype == torch.float32 else QG_FP64), 1, a
+    x = np.asarray(a)
+    if x.dtype != np.float32:
+        x = x.astype(np.float64)
+    x = np.ascontiguousarray(x)
+    nsnap = x.shape[0]
+    return x.ctypes.data, nsnap, x.size // max(nsnap, 1), (QG_FP32 if x.dtype == np.float32 else QG_FP64), 0, x
+
+
+def qg_series_compare(les, ff, lag_min: int, lag_max: int, stream=None):
+    """Lag table of two snapshot series (Eq. 15-16): dist, pcc (n_ff, nlag), mean_dist (nlag,), phase.
+
+    ``les`` and ``ff`` are (nsnap, ...) arrays of one dtype: both numpy (host)
+    or both torch CUDA tensors (device).
+    """
+    pa, na, npa, da, dev_a, ka = _series(les)
+    pb, nb, npb, db, dev_b, kb = _series(ff)
+    if npa != npb or da != db or dev_a != dev_b:
+        raise ValueError("series must have the same field size, dtype and location")
+    nlag = int(lag_max) - int(lag_min) + 1
+    dist = np.empty((nb, max(nlag, 0)))
+    pcc = np.empty((nb, max(nlag, 0)))
+    mean = np.empty(max(nlag, 0))
+    phase = C.c_int32(0)
+    P = C.POINTER(C.c_double)
+    rc = load().qg_series_compare(pa, na, pb, nb, npa, da, dev_a, int(lag_min), int(lag_max), _stream_ptr(stream),
+                                  dist.ctypes.data_as(P), pcc.ctypes.data_as(P), mean.ctypes.data_as(P),
+                                  C.byref(phase))
+    check(rc, "qg_series_compare")
+    del ka, kb
+    return {"dist": dist, "pcc": pcc, "mean_dist": mean, "phase": phase.value}
 
 
 @dataclass
