@@ -305,6 +305,12 @@ template <> struct FInvK2<float> {
   }
 };
 
+// modes per batch in the column pass's state update (loads of a batch precede its stores)
+#ifndef QG_STATE_BATCH
+#define QG_STATE_BATCH 8
+#endif
+constexpr int kStateBatch = QG_STATE_BATCH;
+
 template <typename T, int N, int OP>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(
     Geom g, ColDesc d, const cplx_t<T>* __restrict__ tw, const __grid_constant__ TmaSet tm) {
@@ -505,84 +511,130 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
       coeff = T(red[0][0]);
     }
 
-    // ---- new state per owned mode (registers A)
+    // ---- new state per owned mode (registers A).  The modes go in batches
+    // of GB whose global loads are all issued before any of the batch's
+    // stores: the state arrays may alias as far as the compiler can tell, so
+    // a load placed after a store would wait for that store's round trip.
     const T dt = T(d.dt), a_rk = T(d.a), b_rk = T(d.b), beta = T(d.beta);
     const T* vx = reinterpret_cast<const T*>(d.visc_x);
     const T* vy = reinterpret_cast<const T*>(d.visc_y);
     const T vmu = T(d.visc_mu);
+    const C* bhp = reinterpret_cast<const C*>(d.bh);
+    C* ep = reinterpret_cast<C*>(d.eprev);
+    C* wsp = reinterpret_cast<C*>(d.wss);
+    constexpr int GB = kStateBatch;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int k = t + TT * m;
-      const bool kept = (k <= K || k >= N - K) && col_ok;
-      const int r = k <= K ? k : k - N + Ny;
-      const int my = k <= K ? k : k - N;
-      C wn = mk<C>(T(0), T(0));
-      if (kept) {
+    for (int m0 = 0; m0 < 16; m0 += GB) {
+      // per op: u0 = w^n (or w* in the AB2CN final), u1 = stage field or E_prev,
+      // u2 = J, u3 = D, u4 = Brinkman forcing, u5 = previous w*; vf = viscous factor
+      C u0[GB], u1[GB], u2[GB], u3[GB], u4[GB], u5[GB];
+      T vf[GB];
+#pragma unroll
+      for (int q = 0; q < GB; ++q) {
+        const int k = t + TT * (m0 + q);
+        const bool kept = (k <= K || k >= N - K) && col_ok;
+        const int r = k <= K ? k : k - N + Ny;
         const size_t gi = colbase + r;
-        if constexpr (OP == CO_DERIVE) {
-          wn = w0[gi];
-        } else if constexpr (OP == CO_STAGE_STATIC || OP == CO_DYN_COMBINE) {
-          const C wz = w0[gi];
-          const C wst = d.use_ws ? ws[gi] : wz;
-          const T ik2 = FInvK2<T>::get(ks2, mx * mx + my * my);
-          const C psi = mk<C>(-wst.x * ik2, -wst.y * ik2);
-          const C bv = cscale(cmul_ik(psi, kxv), beta);
-          C L;
-          if constexpr (OP == CO_STAGE_STATIC) {
-            L = csub(A[m], bv);
-            if (d.nfwd > 1) L = cadd(L, cscale(B[m], coeff));
-          } else {
-            const C J = jh[gi];
-            L = csub(mk<C>(-J.x, -J.y), bv);
-            L = cadd(L, cscale(dh[gi], coeff));
+        const C z = mk<C>(T(0), T(0));
+        u0[q] = z; u1[q] = z; u2[q] = z; u3[q] = z; u4[q] = z; u5[q] = z;
+        vf[q] = T(1);
+        if (kept) {
+          if constexpr (OP == CO_DERIVE) {
+            u0[q] = w0[gi];
+          } else if constexpr (OP == CO_STAGE_STATIC || OP == CO_DYN_COMBINE) {
+            u0[q] = w0[gi];
+            u1[q] = d.use_ws ? ws[gi] : u0[q];
+            if constexpr (OP == CO_DYN_COMBINE) {
+              u2[q] = jh[gi];
+              u3[q] = dh[gi];
+            }
+          } else if constexpr (OP == CO_AB2CN || OP == CO_AB2CN_COMBINE) {
+            u0[q] = w0[gi];
+            if constexpr (OP == CO_AB2CN_COMBINE) {
+              u2[q] = jh[gi];
+              u3[q] = dh[gi];
+              if (d.brink) u4[q] = bhp[gi];
+            }
+            if (!d.ab2_first) {
+              u1[q] = ep[gi];
+              if (d.sponge_next) u5[q] = wsp[gi];
+            }
+          } else if constexpr (OP == CO_AB2CN_FINAL) {
+            u0[q] = wsp[gi];
           }
-          const C inner = cadd(wst, cscale(L, dt));
-          wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
-        } else if constexpr (OP == CO_AB2CN || OP == CO_AB2CN_COMBINE) {
-          // Eq. 4: w* = ((1 + dt/2 lin) w^t + dt (3/2 E - 1/2 E_prev)) / (1 - dt/2 lin)
-          C E;
-          if constexpr (OP == CO_AB2CN) {
-            E = (d.nst > 1) ? cadd(A[m], cscale(B[m], coeff)) : A[m];
-          } else {
-            const C J = jh[gi];
-            E = cadd(mk<C>(-J.x, -J.y), cscale(dh[gi], coeff));
-            if (d.brink) E = cadd(E, reinterpret_cast<const C*>(d.bh)[gi]);
-          }
-          C* ep = reinterpret_cast<C*>(d.eprev);
-          const C Ep = d.ab2_first ? E : ep[gi];
-          ep[gi] = E;
-          const int m2 = mx * mx + my * my;
-          const T k2 = T(ks2) * T(m2);
-          const T ik2 = FInvK2<T>::get(ks2, m2);
-          const T hdt = T(0.5) * dt;
-          const T lre = -(T(d.nu) * k2 + T(d.mu));
-          const T lim = beta * kxv * ik2;
-          const C wz = w0[gi];
-          const C ab = mk<C>(T(1.5) * E.x - T(0.5) * Ep.x, T(1.5) * E.y - T(0.5) * Ep.y);
-          const C num = cadd(cmul(mk<C>(T(1) + hdt * lre, hdt * lim), wz), cscale(ab, dt));
-          const T dre = T(1) - hdt * lre, dim = -hdt * lim;
-          const T den = dre * dre + dim * dim;
-          const C wst = mk<C>((num.x * dre + num.y * dim) / den, (num.y * dre - num.x * dim) / den);
-          if (d.sponge_next) {
-            C* wsp = reinterpret_cast<C*>(d.wss);
-            const C wss = d.ab2_first ? wst : wsp[gi];
-            wsp[gi] = wst;
-            wn = mk<C>(T(1.5) * wst.x - T(0.5) * wss.x, T(1.5) * wst.y - T(0.5) * wss.y);
-          } else {
-            wn = wst;
-          }
-        } else if constexpr (OP == CO_AB2CN_FINAL) {
-          const C wst = reinterpret_cast<const C*>(d.wss)[gi];
-          wn = csub(wst, A[m]);
-        } else {
-          wn = A[m];
+          if (d.viscous) vf[q] = vx[mx] * vy[r] * vmu;
         }
-        if (d.viscous) wn = cscale(wn, vx[mx] * vy[r] * vmu);
-        if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
-        if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
-        if (d.store_w0) w0[gi] = wn;
       }
-      A[m] = wn;
+#pragma unroll
+      for (int q = 0; q < GB; ++q) {
+        const int m = m0 + q;
+        const int k = t + TT * m;
+        const bool kept = (k <= K || k >= N - K) && col_ok;
+        const int r = k <= K ? k : k - N + Ny;
+        const int my = k <= K ? k : k - N;
+        C wn = mk<C>(T(0), T(0));
+        if (kept) {
+          const size_t gi = colbase + r;
+          if constexpr (OP == CO_DERIVE) {
+            wn = u0[q];
+          } else if constexpr (OP == CO_STAGE_STATIC || OP == CO_DYN_COMBINE) {
+            const C wz = u0[q];
+            const C wst = u1[q];
+            const T ik2 = FInvK2<T>::get(ks2, mx * mx + my * my);
+            const C psi = mk<C>(-wst.x * ik2, -wst.y * ik2);
+            const C bv = cscale(cmul_ik(psi, kxv), beta);
+            C L;
+            if constexpr (OP == CO_STAGE_STATIC) {
+              L = csub(A[m], bv);
+              if (d.nfwd > 1) L = cadd(L, cscale(B[m], coeff));
+            } else {
+              L = csub(mk<C>(-u2[q].x, -u2[q].y), bv);
+              L = cadd(L, cscale(u3[q], coeff));
+            }
+            const C inner = cadd(wst, cscale(L, dt));
+            wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
+          } else if constexpr (OP == CO_AB2CN || OP == CO_AB2CN_COMBINE) {
+            // Eq. 4: w* = ((1 + dt/2 lin) w^t + dt (3/2 E - 1/2 E_prev)) / (1 - dt/2 lin)
+            C E;
+            if constexpr (OP == CO_AB2CN) {
+              E = (d.nst > 1) ? cadd(A[m], cscale(B[m], coeff)) : A[m];
+            } else {
+              E = cadd(mk<C>(-u2[q].x, -u2[q].y), cscale(u3[q], coeff));
+              if (d.brink) E = cadd(E, u4[q]);
+            }
+            const C Ep = d.ab2_first ? E : u1[q];
+            ep[gi] = E;
+            const int m2 = mx * mx + my * my;
+            const T k2 = T(ks2) * T(m2);
+            const T ik2 = FInvK2<T>::get(ks2, m2);
+            const T hdt = T(0.5) * dt;
+            const T lre = -(T(d.nu) * k2 + T(d.mu));
+            const T lim = beta * kxv * ik2;
+            const C wz = u0[q];
+            const C ab = mk<C>(T(1.5) * E.x - T(0.5) * Ep.x, T(1.5) * E.y - T(0.5) * Ep.y);
+            const C num = cadd(cmul(mk<C>(T(1) + hdt * lre, hdt * lim), wz), cscale(ab, dt));
+            const T dre = T(1) - hdt * lre, dim = -hdt * lim;
+            const T den = dre * dre + dim * dim;
+            const C wst = mk<C>((num.x * dre + num.y * dim) / den, (num.y * dre - num.x * dim) / den);
+            if (d.sponge_next) {
+              const C wss = d.ab2_first ? wst : u5[q];
+              wsp[gi] = wst;
+              wn = mk<C>(T(1.5) * wst.x - T(0.5) * wss.x, T(1.5) * wst.y - T(0.5) * wss.y);
+            } else {
+              wn = wst;
+            }
+          } else if constexpr (OP == CO_AB2CN_FINAL) {
+            wn = csub(u0[q], A[m]);
+          } else {
+            wn = A[m];
+          }
+          if (d.viscous) wn = cscale(wn, vf[q]);
+          if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
+          if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
+          if (d.store_w0) w0[gi] = wn;
+        }
+        A[m] = wn;
+      }
     }
 
     // ---- derived fields, inverse y-transforms, mixed arrays out.
