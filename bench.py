@@ -39,6 +39,7 @@ WORKLOADS = {
 
 METRIC = "grid-pt-steps/s at 2048^2 dyn-Leith, FP32 vs FP64 at stated err; % HBM peak"
 UNIT = "grid-pt-steps/s"
+SCHEMES = {"rk3": 0, "ab2cn": 1}
 
 
 def dist_env():
@@ -111,6 +112,45 @@ def algorithmic_bytes(wl, precision_fp32: bool):
     return out
 
 
+def algorithmic_bytes_ab2cn(wl, precision_fp32: bool):
+    """Minimal HBM bytes per launch of each kernel class of one AB2CN step (Eq. 4), steady state.
+
+    Same units as ``algorithmic_bytes``.  One explicit evaluation per step:
+    row pass (products), Brinkman row pass (chi u), Germano reduction writing
+    J, D (and the Brinkman forcing) spectra, the AB2CN combine (reads E_prev
+    and writes E, reads w^n, and with a sponge reads/writes the w* history and
+    writes the field the sponge row pass needs), sponge row pass, final pass.
+    """
+    n = wl.n
+    K = (n - 1) // 3
+    esz = 4 if precision_fp32 else 8
+    I = n * (K + 1) * 2 * esz
+    Sp = (K + 1) * (2 * K + 1) * 2 * esz
+    R = n * n * esz
+    kind = wl.closure
+    nin = {S.NONE: 4, S.LEITH: 4, S.SMAG: 6, S.DLEITH: 8, S.DSMAG: 12}[kind]
+    nout = {S.NONE: 1, S.LEITH: 3, S.SMAG: 3, S.DLEITH: 6, S.DSMAG: 6}[kind]
+    dyn = kind in (S.DSMAG, S.DLEITH)
+    mask = wl.geometry != "none"
+    sponge = wl.sponge
+    out = {"row_stage": (1, (nin + nout) * I)}
+    if mask:
+        out["row_brinkman"] = (1, 4 * I + R)
+    if dyn:
+        out["col_reduce"] = (1, (nout + (2 if mask else 0)) * I + (3 if mask else 2) * Sp)
+        forcing = (3 if mask else 2) * Sp
+    else:
+        forcing = (nout + (2 if mask else 0)) * I
+    combine = forcing + 2 * Sp + Sp  # E_prev read + write, w^n read
+    if sponge:
+        out["col_stage"] = (1, combine + 2 * Sp + I)  # w* history read + write, the sponge's field
+        out["row_sponge"] = (1, 2 * I + R)
+        out["col_final"] = (1, I + Sp + Sp + nin * I)  # forcing, w*, w^{n+1}, next step's fields
+    else:
+        out["col_final"] = (1, combine + Sp + nin * I)
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -168,11 +208,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def time_oracle(wl, max_seconds: float, warmup: int = 1):
+def time_oracle(wl, max_seconds: float, warmup: int = 1, scheme: int = 0):
     """The FP64 CPU oracle, as it stands, on the workload; bounded wall time."""
     import oracle as O
     ref = O.QGOracle(wl.n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure, c=wl.c),
-                     O.Params(dt=wl.dt, nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate))
+                     O.Params(dt=wl.dt, nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, scheme=scheme))
     ref.set_state(wl.omega0())
     for _ in range(warmup):
         ref.step(1)
@@ -192,18 +232,195 @@ def run_reference(args, wl):
     if rank != 0:
         return
     budget = float(os.environ.get("QG_REF_SECONDS", "60"))
-    steps, el = time_oracle(wl, budget, warmup=min(args.warmup, 1))
+    if args.workload in TOOLS:
+        TOOLS[args.workload]["reference"](args, budget)
+        return
+    steps, el = time_oracle(wl, budget, warmup=min(args.warmup, 1), scheme=SCHEMES[args.scheme])
     value = wl.n * wl.n * steps / el
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": steps,
         "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure]},
+        "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure], "scheme": args.scheme,
+                   "eta": wl.eta},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{steps} full {wl.n}^2 steps of the FP64 numpy oracle (bounded to ~{budget:.0f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# A posteriori lag table (Eq. 15-16): qg_series_compare on two FP32 snapshot
+# series of 512^2 fields, 96 snapshots each, lags -32 .. 32.
+# ---------------------------------------------------------------------------
+SERIES = {"n": 512, "nsnap": 96, "lag": 32, "seed": 21, "dt_snap": 0.1, "shift": 3}
+SERIES_METRIC = "pair-points/s of the Eq. 15-16 lag table, 512^2 FP32 series, 96 snapshots, lags -32..32"
+SERIES_UNIT = "pair-points/s"
+# FP32-pipe instructions per (pair, point) in the pairs kernel: the difference
+# and its compensated square (1 + 10), the two centred values and their
+# compensated product (2 + 10)
+SERIES_INST = 23
+
+
+def series_inputs():
+    c = SERIES
+    L = 2 * math.pi
+    ff = S.wave_series(c["seed"], c["n"], c["nsnap"], L, dt_snap=c["dt_snap"], noise=0.2).astype(np.float32)
+    les = S.wave_series(c["seed"], c["n"], c["nsnap"], L, dt_snap=c["dt_snap"], t0=c["shift"] * c["dt_snap"],
+                        noise=0.2, noise_seed=c["seed"] + 100).astype(np.float32)
+    return les, ff
+
+
+def valid_pairs(n_les: int, n_ff: int, lag_min: int, lag_max: int) -> int:
+    """Number of (t, phi) with 0 <= t - phi < n_les, t < n_ff, lag_min <= phi <= lag_max."""
+    return sum(1 for t in range(n_ff) for phi in range(lag_min, lag_max + 1) if 0 <= t - phi < n_les)
+
+
+def time_series_oracle(les, ff, max_seconds: float):
+    """The oracle's lag table, one pair at a time over the workload's pairs, bounded wall time."""
+    import oracle as O
+    lag = SERIES["lag"]
+    pairs = [(t, phi) for t in range(len(ff)) for phi in range(-lag, lag + 1) if 0 <= t - phi < len(les)]
+    rng = np.random.default_rng(0)
+    order = rng.permutation(len(pairs))
+    done = 0
+    t0 = time.perf_counter()
+    for k in order:
+        t, phi = pairs[k]
+        O.lag_table(les[t - phi:t - phi + 1].astype(np.float64), ff[t:t + 1].astype(np.float64), 0, 0)
+        done += 1
+        if time.perf_counter() - t0 >= max_seconds:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_series_reference(args, budget):
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    les, ff = series_inputs()
+    npts = les[0].size
+    pairs, el = time_series_oracle(les, ff, budget)
+    value = pairs * npts / el
+    line = {
+        "metric": SERIES_METRIC, "value": value, "unit": SERIES_UNIT, "impl": "reference", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * el, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "series512", **SERIES},
+        "cpu_baseline": {"value": value, "unit": SERIES_UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{pairs} (snapshot, lag) pairs of 512^2 fields by the FP64 numpy oracle "
+                                   f"(bounded to ~{budget:.0f} s)"},
+        "e2e": {"value": value, "unit": SERIES_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_series_bench(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2508_06678_gb300 as qg
+    from paper_2508_06678_gb300._lib import LIB_PATH, load
+    if not os.path.exists(LIB_PATH):
+        from paper_2508_06678_gb300.build import build
+        build()
+    load()
+
+    les, ff = series_inputs()
+    npts = les[0].size
+    lag_min, lag_max = -SERIES["lag"], SERIES["lag"]
+    nlag = lag_max - lag_min + 1
+    pp = valid_pairs(len(les), len(ff), lag_min, lag_max) * npts  # pair-points per call
+    stream = torch.cuda.Stream()
+    dl = torch.from_numpy(les).cuda()
+    df = torch.from_numpy(ff).cuda()
+    torch.cuda.synchronize()
+
+    def call(timing=False):
+        return qg.qg_series_compare(dl, df, lag_min, lag_max, stream=stream, timing=timing)
+
+    for _ in range(args.warmup):
+        r = call()
+    phase = r["phase"]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except (AttributeError, RuntimeError):
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        call()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    value = world * pp / (ms / 1e3)
+
+    # kernel durations (CUDA events inside the call, on its stream)
+    kms = [call(timing=True)["kernel_ms"] for _ in range(args.steps)]
+    avg = {k: sum(d[k] for d in kms) / len(kms) for k in kms[0]}
+    props = torch.cuda.get_device_properties(local)
+    nsm = props.multi_processor_count
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = nsm * 128 * sm_mhz * 1e6 / 1e12  # FP32-pipe instructions, Tinst/s
+    achieved = pp * SERIES_INST / (avg["pairs"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s (FP32 pipe)",
+                "frac": achieved / peak, "traffic": None, "kernel": "series_pairs_kernel",
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                "inst_per_pair_point": SERIES_INST, "avg_launch_us": avg["pairs"] * 1e3,
+                "kernel_ms": avg,
+                "measured_in": "CUDA events around each kernel group inside the call, second pass"}
+
+    # end to end with host series (copies inside the call)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        qg.qg_series_compare(les, ff, lag_min, lag_max, stream=stream)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": world * pp / e2e_s, "unit": SERIES_UNIT, "h2d_bytes_per_step": les.nbytes + ff.nbytes,
+           "d2h_bytes_per_step": (2 * len(ff) * nlag + nlag) * 8 + 4,
+           "api": "qg_series_compare(host series)"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            pairs_c, el_c = time_series_oracle(les, ff, args.cpu_seconds)
+            cpu = {"value": pairs_c * npts / el_c, "unit": SERIES_UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{pairs_c} (snapshot, lag) pairs of 512^2 fields by the FP64 numpy oracle, {el_c:.1f} s"}
+        line = {
+            "metric": SERIES_METRIC, "value": value, "unit": SERIES_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "series512", **SERIES, "pair_points_per_call": pp, "phase": phase,
+                       "l2": "two 100 MB series, 201 MB > 126 MB L2 (no flush)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+TOOLS = {"series512": {"ours": run_series_bench, "reference": run_series_reference}}
 
 
 def main():
@@ -212,7 +429,9 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=1000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="island2048-dleith", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="island2048-dleith", choices=sorted(WORKLOADS) + sorted(TOOLS))
+    ap.add_argument("--scheme", default="rk3", choices=sorted(SCHEMES),
+                    help="time scheme: rk3 (SSP-RK3 with exact sub-steps) or ab2cn (the paper's Eq. 4)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -220,12 +439,22 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--err-steps", type=int, default=100)
     args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        raise SystemExit("--warmup must be >= 3")
+    if args.workload in TOOLS:
+        if args.impl == "reference":
+            run_reference(args, None)
+        else:
+            TOOLS[args.workload]["ours"](args)
+        return
     wl = WORKLOADS[args.workload]()
+    if args.scheme == "ab2cn":
+        # AB2 treats the Brinkman term explicitly, which is stable only for
+        # eta > dt (Sec. II-E); the paper's runs use eta = 1.025 dt
+        wl.eta = 1.025 * wl.dt
     if args.impl == "reference":
         run_reference(args, wl)
         return
-    if args.warmup < 3:
-        raise SystemExit("--warmup must be >= 3")
 
     import torch
     import torch.distributed as dist
@@ -246,7 +475,9 @@ def main():
 
     fp32 = args.precision == "fp32"
     stream = torch.cuda.Stream()
-    solver = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32 if fp32 else qg.QG_FP64, stream=stream)
+    scheme = SCHEMES[args.scheme]
+    solver = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32 if fp32 else qg.QG_FP64, stream=stream,
+                                       scheme=scheme)
     w0 = wl.omega0()
     solver.set_state(w0)
     solver.step(args.warmup)
@@ -297,7 +528,7 @@ def main():
 
     # ---- roofline of the dominant kernel class
     peaks, peak_src = measured_peaks()
-    model = algorithmic_bytes(wl, fp32)
+    model = algorithmic_bytes(wl, fp32) if scheme == 0 else algorithmic_bytes_ab2cn(wl, fp32)
     per_class = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(8)}
     dom = max((k for k in per_class if per_class[k][0] > 0 and k in model), key=lambda k: per_class[k][1])
     n_l, t_l = per_class[dom]
@@ -348,7 +579,7 @@ def main():
     # relative vorticity error against it after the same number of steps
     fp64 = None
     if fp32 and not args.no_fp64:
-        s64 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP64, stream=stream)
+        s64 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP64, stream=stream, scheme=scheme)
         s64.set_state(w0)
         s64.step(5)
         s64.sync()
@@ -360,7 +591,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / k64
-        s32 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32, stream=stream)
+        s32 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32, stream=stream, scheme=scheme)
         s64.set_state(w0)
         s32.set_state(w0)
         s64.step(args.err_steps)
@@ -381,7 +612,7 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            steps_c, el_c = time_oracle(wl, args.cpu_seconds, warmup=0)
+            steps_c, el_c = time_oracle(wl, args.cpu_seconds, warmup=0, scheme=scheme)
             cpu = {"value": wl.n * wl.n * steps_c / el_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{steps_c} full {wl.n}^2 step(s) of the FP64 numpy oracle (single-threaded), "
                              f"{el_c:.1f} s"}
@@ -389,8 +620,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure],
-                       "geometry": wl.geometry, "beta": wl.beta, "U": wl.U, "dt": wl.dt,
+            "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure], "scheme": args.scheme,
+                       "geometry": wl.geometry, "beta": wl.beta, "U": wl.U, "dt": wl.dt, "eta": wl.eta,
                        "precision": args.precision + (" (FP64 Germano sums, diagnostics, low-k inversion)"
                                                       if fp32 else ""),
                        "parallelism": f"replicas{world}" if world > 1 else "single",

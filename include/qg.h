@@ -185,7 +185,7 @@ int qg_grid_filter(const double* omega_fr, int32_t nsnap, int32_t n_fr, int32_t 
 
 /* A posteriori comparison of two snapshot series on one grid (Sec. IV,
  * Eq. 15 and 16).
- *   les: n_les_snap fields, ff: n_ff_snap fields (1 .. 2^20 each), npts >= 1
+ *   les: n_les_snap fields, ff: n_ff_snap fields (1 .. 10^6 each), npts >= 1
  *        values per field, snapshot-major and contiguous; dtype QG_FP32 or
  *        QG_FP64 for both; on_device = 1: device pointers (borrowed, read
  *        only, used on stream), 0: host pointers (copied to the device).
@@ -202,13 +202,16 @@ int qg_grid_filter(const double* omega_fr, int32_t nsnap, int32_t n_fr, int32_t 
  *        defined entries (NaN if none);
  *   phase or NULL: the lag of Eq. 16, the phi of the smallest mean_dist
  *        (ties: the smallest |phi|, then the negative lag).
+ *   kernel_ms[4] or NULL: device milliseconds of the call's four kernel
+ *        groups (moments, pairs, finish, phase), from CUDA events recorded
+ *        on stream around them (-1 where an event could not be made).
  * QG_ERR_ARG if no lag in the range pairs two snapshots.  FP32 series are
  * differenced and multiplied in FP32 with each thread's sums compensated,
  * chunk sums and all means in FP64; FP64 series run in FP64.  Deterministic;
  * synchronous; allocates its scratch per call. */
 int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32_t n_ff_snap, int64_t npts,
                       int32_t dtype, int32_t on_device, int32_t lag_min, int32_t lag_max, void* stream, double* dist,
-                      double* pcc, double* mean_dist, int32_t* phase);
+                      double* pcc, double* mean_dist, int32_t* phase, double* kernel_ms);
 
 /* Kernel classes reported by qg_kernel_times. */
 #define QG_K_ROW_STAGE 0   /* row pass of an RK stage (products of Eq. 1, 9-14) */

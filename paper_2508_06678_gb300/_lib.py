@@ -66,7 +66,7 @@ SIGNATURES = {
                                  C.POINTER(qg_params), C.c_double, C.c_double, C.c_int32, DP, DP, DP, DP]),
     "qg_grid_filter": (C.c_int, [DP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, DP]),
     "qg_series_compare": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
-                                    C.c_int32, C.c_int32, C.c_void_p, DP, DP, DP, C.POINTER(C.c_int32)]),
+                                    C.c_int32, C.c_int32, C.c_void_p, DP, DP, DP, C.POINTER(C.c_int32), DP]),
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int32]),
     "qg_field_stats_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),

@@ -8,7 +8,8 @@
 // negative lag).
 //
 // Kernels (all reductions in a fixed order, so results are deterministic):
-//   moments   one CTA per snapshot: mean and centred sum of squares, FP64
+//   moments   (chunk, snapshot) CTAs: chunk sums, then chunk sums of squares
+//             about the mean (compensated per thread for FP32 fields)
 //   pairs     a 16 x 16 tile of (t, phi) pairs per CTA, one pair per thread,
 //             over one chunk of the points; the 16 ff rows and the 31 les
 //             rows the tile needs are staged through shared memory (rows
@@ -33,7 +34,7 @@ constexpr int kTileT = 16;                   // ff snapshots per tile
 constexpr int kTileL = 16;                   // lags per tile
 constexpr int kRowsA = kTileT + kTileL - 1;  // les rows a tile touches
 constexpr int kThreads = kTileT * kTileL;
-constexpr int kMaxSnap = 1 << 20;
+constexpr int kMaxSnap = 1000000;  // keeps the pair grid's y extent (snapshots / 16) within 65535
 constexpr int kMaxLag = 1 << 16;
 constexpr size_t kMaxPairs = size_t(1) << 24;
 constexpr size_t kPartialBytes = size_t(256) << 20;
@@ -54,29 +55,87 @@ __device__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// mean and centred sum of squares of each snapshot (FP64, two passes)
+// Per-snapshot moments in two passes over a grid of (chunk, snapshot) CTAs,
+// snapshots 0 .. n_a - 1 from series a and the rest from series b.
+// Pass 1 writes each chunk's sum; pass 2 forms the mean from those sums (a
+// fixed-order warp reduction, identical in every CTA of the snapshot) and
+// writes each chunk's sum of (x - m_c)^2 about the mean rounded to the
+// working precision, m_c.  Per-thread sums are compensated for FP32 fields.
+struct MomArgs {
+  int n_a, nsnap, nchunk;
+  int64_t npts, chunk;
+  double* sum_part;  // [snap][chunk]
+  double* sq_part;   // [snap][chunk]
+  double* mean;      // [snap]
+};
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) series_moments_kernel(const T* __restrict__ x, int64_t npts,
-                                                                  double* mean, double* css) {
+__device__ const T* snapshot(const T* a, const T* b, const MomArgs& A, int s) {
+  return s < A.n_a ? a + (size_t)s * (size_t)A.npts : b + (size_t)(s - A.n_a) * (size_t)A.npts;
+}
+
+template <typename T> struct SumAcc;
+template <> struct SumAcc<double> {
+  double s = 0.0;
+  __device__ void add(double x) { s += x; }
+  __device__ double value() const { return s; }
+};
+template <> struct SumAcc<float> {
+  GermanoAcc<float> g;
+  __device__ void add(float x) { g.add(x); }
+  __device__ double value() const { return g.value(); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) series_sum_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                                              MomArgs A) {
+  __shared__ double red[kThreads / 32];
+  const int snap = blockIdx.x;
+  const T* f = snapshot(a, b, A, snap);
+  const int64_t p0 = (int64_t)blockIdx.y * A.chunk;
+  const int64_t p1 = p0 + A.chunk < A.npts ? p0 + A.chunk : A.npts;
+  SumAcc<T> acc;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) acc.add(f[p]);
+  const double v = block_sum(acc.value(), red);
+  if (threadIdx.x == 0) A.sum_part[(size_t)snap * A.nchunk + blockIdx.y] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) series_sq_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                                             MomArgs A) {
   __shared__ double red[kThreads / 32];
   __shared__ double m_sh;
-  const T* f = x + (size_t)blockIdx.x * (size_t)npts;
-  double s = 0.0;
-  for (int64_t p = threadIdx.x; p < npts; p += blockDim.x) s += double(f[p]);
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) m_sh = s / double(npts);
+  const int snap = blockIdx.x;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < A.nchunk; c += 32) s += A.sum_part[(size_t)snap * A.nchunk + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+      m_sh = s / double(A.npts);
+      if (blockIdx.y == 0) A.mean[snap] = m_sh;
+    }
+  }
   __syncthreads();
-  const double m = m_sh;
+  const T mc = T(m_sh);
+  const T* f = snapshot(a, b, A, snap);
+  const int64_t p0 = (int64_t)blockIdx.y * A.chunk;
+  const int64_t p1 = p0 + A.chunk < A.npts ? p0 + A.chunk : A.npts;
+  GermanoAcc<T> acc;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+    const T d = f[p] - mc;
+    acc.add_prod(d, d);
+  }
+  const double v = block_sum(acc.value(), red);
+  if (threadIdx.x == 0) A.sq_part[(size_t)snap * A.nchunk + blockIdx.y] = v;
+}
+
+// centred sum of squares of one snapshot: the chunks' sums about m_c, less n (m - m_c)^2
+__device__ double snapshot_css(const MomArgs& M, int snap, int fp32) {
   double q = 0.0;
-  for (int64_t p = threadIdx.x; p < npts; p += blockDim.x) {
-    const double d = double(f[p]) - m;
-    q = fma(d, d, q);
-  }
-  q = block_sum(q, red);
-  if (threadIdx.x == 0) {
-    mean[blockIdx.x] = m;
-    css[blockIdx.x] = q;
-  }
+  for (int c = 0; c < M.nchunk; ++c) q += M.sq_part[(size_t)snap * M.nchunk + c];
+  const double m = M.mean[snap];
+  const double mc = fp32 ? double(float(m)) : m;
+  return q - double(M.npts) * (m - mc) * (m - mc);
 }
 
 struct PairArgs {
@@ -141,10 +200,7 @@ struct FinishArgs {
   int n_les, n_ff, lag_min, nlag, nchunk, fp32;
   int64_t npts;
   const double* part;
-  const double* mean_les;
-  const double* css_les;
-  const double* mean_ff;
-  const double* css_ff;
+  MomArgs mom;  // snapshots 0 .. n_les - 1 are les, then ff
   double* dist;
   double* pcc;
 };
@@ -167,11 +223,11 @@ __global__ void series_finish_kernel(FinishArgs A) {
   }
   // the pairs kernel centred on the means rounded to the working precision:
   // sum (a - a_c)(b - b_c) = sum (a - mean_a)(b - mean_b) + n (mean_a - a_c)(mean_b - b_c)
-  const double ma = A.mean_les[s], mb = A.mean_ff[t];
+  const double ma = A.mom.mean[s], mb = A.mom.mean[A.n_les + t];
   const double ca = A.fp32 ? double(float(ma)) : ma, cb = A.fp32 ? double(float(mb)) : mb;
   cr -= double(A.npts) * (ma - ca) * (mb - cb);
   A.dist[idx] = d2;
-  const double va = A.css_les[s], vb = A.css_ff[t];
+  const double va = snapshot_css(A.mom, s, A.fp32), vb = snapshot_css(A.mom, A.n_les + t, A.fp32);
   A.pcc[idx] = (va > 0.0 && vb > 0.0) ? cr / (sqrt(va) * sqrt(vb)) : NAN;
 }
 
@@ -231,20 +287,56 @@ struct Scratch {
   }
 };
 
+// Optional CUDA-event brackets around the call's kernels (moments, pairs, finish, phase).
+struct Timer {
+  cudaEvent_t ev[5] = {};
+  bool on = false;
+  cudaStream_t st = nullptr;
+  void start(bool enable, cudaStream_t s) {
+    st = s;
+    on = enable;
+    for (int i = 0; on && i < 5; ++i) on = cudaEventCreate(&ev[i]) == cudaSuccess;
+  }
+  void mark(int i) {
+    if (on) cudaEventRecord(ev[i], st);
+  }
+  void read(double* ms) {
+    for (int i = 0; i < 4; ++i) {
+      float v = 0.f;
+      ms[i] = (on && cudaEventElapsedTime(&v, ev[i], ev[i + 1]) == cudaSuccess) ? double(v) : -1.0;
+    }
+  }
+  ~Timer() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 template <typename T>
 cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t npts, int lag_min, int nlag,
-                        cudaStream_t st, Scratch& S, double* d_dist, double* d_pcc, double* d_mean, int* d_phase) {
-  double* mom = static_cast<double*>(S.get(sizeof(double) * 2 * (size_t)(n_les + n_ff)));
-  if (!mom) return S.err;
-  double *mean_les = mom, *css_les = mom + n_les, *mean_ff = mom + 2 * n_les, *css_ff = mean_ff + n_ff;
-  series_moments_kernel<T><<<n_les, kThreads, 0, st>>>(les, npts, mean_les, css_les);
-  series_moments_kernel<T><<<n_ff, kThreads, 0, st>>>(ff, npts, mean_ff, css_ff);
-
-  // split the points into chunks: a few waves of CTAs over the SMs, partials within budget
-  const int tiles_t = (n_ff + kTileT - 1) / kTileT, tiles_l = (nlag + kTileL - 1) / kTileL;
+                        cudaStream_t st, Scratch& S, Timer& tm, double* d_dist, double* d_pcc, double* d_mean,
+                        int* d_phase) {
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // moments: a few waves of (chunk, snapshot) CTAs, at least 1024 points per CTA
+  const int nsnap = n_les + n_ff;
+  int64_t mchunks = (4 * (int64_t)nsm + nsnap - 1) / nsnap;
+  const int64_t max_mchunks = (npts + 1023) / 1024;
+  if (mchunks > max_mchunks) mchunks = max_mchunks;
+  if (mchunks > 65535) mchunks = 65535;
+  if (mchunks < 1) mchunks = 1;
+  const int64_t mchunk = (npts + mchunks - 1) / mchunks;
+  mchunks = (npts + mchunk - 1) / mchunk;
+  double* mbuf = static_cast<double*>(S.get(sizeof(double) * ((size_t)2 * nsnap * mchunks + nsnap)));
+  if (!mbuf) return S.err;
+  MomArgs M{n_les, nsnap, (int)mchunks, npts, mchunk, mbuf, mbuf + (size_t)nsnap * mchunks,
+            mbuf + (size_t)2 * nsnap * mchunks};
+  const double* mean_les = M.mean;
+  const double* mean_ff = M.mean + n_les;
+
+  // split the points into chunks: a few waves of CTAs over the SMs, partials within budget
+  const int tiles_t = (n_ff + kTileT - 1) / kTileT, tiles_l = (nlag + kTileL - 1) / kTileL;
   const int64_t P = Stage<T>::P;
   const int64_t rounds = (npts + P - 1) / P;
   const int64_t tiles = (int64_t)tiles_t * tiles_l;
@@ -258,14 +350,20 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   nchunk = (npts + chunk - 1) / chunk;
   double* part = static_cast<double*>(S.get((size_t)per_chunk_bytes * nchunk));
   if (!part) return S.err;
+  tm.mark(0);
+  series_sum_kernel<T><<<dim3(nsnap, (unsigned)mchunks), kThreads, 0, st>>>(les, ff, M);
+  series_sq_kernel<T><<<dim3(nsnap, (unsigned)mchunks), kThreads, 0, st>>>(les, ff, M);
+  tm.mark(1);
   PairArgs pa{n_les, n_ff, lag_min, nlag, npts, chunk, mean_les, mean_ff, part};
   series_pairs_kernel<T><<<dim3((unsigned)nchunk, tiles_t, tiles_l), kThreads, 0, st>>>(les, ff, pa);
+  tm.mark(2);
 
-  FinishArgs fa{n_les, n_ff, lag_min, nlag, (int)nchunk, sizeof(T) == 4, npts, part, mean_les, css_les,
-                mean_ff, css_ff, d_dist, d_pcc};
+  FinishArgs fa{n_les, n_ff, lag_min, nlag, (int)nchunk, sizeof(T) == 4, npts, part, M, d_dist, d_pcc};
   const size_t npair = (size_t)n_ff * nlag;
   series_finish_kernel<<<(unsigned)((npair + 255) / 256), 256, 0, st>>>(fa);
+  tm.mark(3);
   series_phase_kernel<<<1, 256, 0, st>>>(d_dist, n_ff, nlag, lag_min, d_mean, d_phase);
+  tm.mark(4);
   return cudaGetLastError();
 }
 
@@ -273,7 +371,8 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
 
 extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32_t n_ff_snap,
                                  int64_t npts, int32_t dtype, int32_t on_device, int32_t lag_min, int32_t lag_max,
-                                 void* stream, double* dist, double* pcc, double* mean_dist, int32_t* phase) {
+                                 void* stream, double* dist, double* pcc, double* mean_dist, int32_t* phase,
+                                 double* kernel_ms) {
   char msg[256];
   if (!les || !ff || !dist) return fail(QG_ERR_ARG, "qg_series_compare: NULL argument");
   if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_series_compare: dtype must be QG_FP32 or QG_FP64");
@@ -316,13 +415,15 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
   double* d_out = static_cast<double*>(S.get(sizeof(double) * (2 * npair + nlag)));
   int* d_phase = static_cast<int*>(S.get(2 * sizeof(int)));
   if (!d_out || !d_phase) return fail(QG_ERR_OOM, "qg_series_compare: device allocation failed");
+  Timer tm;
+  tm.start(kernel_ms != nullptr, st);
   cudaError_t e = dtype == QG_FP32
                       ? run_compare<float>(static_cast<const float*>(dl), n_les_snap, static_cast<const float*>(df),
-                                           n_ff_snap, npts, lag_min, nlag, st, S, d_out, d_out + npair,
+                                           n_ff_snap, npts, lag_min, nlag, st, S, tm, d_out, d_out + npair,
                                            d_out + 2 * npair, d_phase)
                       : run_compare<double>(static_cast<const double*>(dl), n_les_snap,
                                             static_cast<const double*>(df), n_ff_snap, npts, lag_min, nlag, st, S,
-                                            d_out, d_out + npair, d_out + 2 * npair, d_phase);
+                                            tm, d_out, d_out + npair, d_out + 2 * npair, d_phase);
   if (e == cudaSuccess) e = S.err;
   if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "qg_series_compare: %s", cudaGetErrorString(e));
@@ -341,6 +442,7 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
   if (pcc) std::copy(h.begin() + npair, h.begin() + 2 * npair, pcc);
   if (mean_dist) std::copy(h.begin() + 2 * npair, h.end(), mean_dist);
   if (phase) *phase = hp[0];
+  if (kernel_ms) tm.read(kernel_ms);
   if (!hp[1]) return fail(QG_ERR_ARG, "qg_series_compare: no lag in the range pairs any two snapshots");
   return QG_OK;
 }

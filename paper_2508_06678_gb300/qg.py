@@ -171,11 +171,12 @@ def _series(a):
     return x.ctypes.data, nsnap, x.size // max(nsnap, 1), (QG_FP32 if x.dtype == np.float32 else QG_FP64), 0, x
 
 
-def qg_series_compare(les, ff, lag_min: int, lag_max: int, stream=None):
+def qg_series_compare(les, ff, lag_min: int, lag_max: int, stream=None, timing: bool = False):
     """Lag table of two snapshot series (Eq. 15-16): dist, pcc (n_ff, nlag), mean_dist (nlag,), phase.
 
     ``les`` and ``ff`` are (nsnap, ...) arrays of one dtype: both numpy (host)
-    or both torch CUDA tensors (device).
+    or both torch CUDA tensors (device).  ``timing`` adds ``kernel_ms``, the
+    device time of the moments, pairs, finish and phase kernels.
     """
     pa, na, npa, da, dev_a, ka = _series(les)
     pb, nb, npb, db, dev_b, kb = _series(ff)
@@ -186,13 +187,17 @@ def qg_series_compare(les, ff, lag_min: int, lag_max: int, stream=None):
     pcc = np.empty((nb, max(nlag, 0)))
     mean = np.empty(max(nlag, 0))
     phase = C.c_int32(0)
+    kms = np.zeros(4)
     P = C.POINTER(C.c_double)
     rc = load().qg_series_compare(pa, na, pb, nb, npa, da, dev_a, int(lag_min), int(lag_max), _stream_ptr(stream),
                                   dist.ctypes.data_as(P), pcc.ctypes.data_as(P), mean.ctypes.data_as(P),
-                                  C.byref(phase))
+                                  C.byref(phase), kms.ctypes.data_as(P) if timing else None)
     check(rc, "qg_series_compare")
     del ka, kb
-    return {"dist": dist, "pcc": pcc, "mean_dist": mean, "phase": phase.value}
+    out = {"dist": dist, "pcc": pcc, "mean_dist": mean, "phase": phase.value}
+    if timing:
+        out["kernel_ms"] = {"moments": kms[0], "pairs": kms[1], "finish": kms[2], "phase": kms[3]}
+    return out
 
 
 @dataclass

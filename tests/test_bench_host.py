@@ -57,3 +57,22 @@ def test_algorithmic_byte_model_production():
     assert m["row_stage"] == (3, 14 * I)
     step = sum(a * b for a, b in m.values())
     assert 1.2e9 < step < 1.3e9
+
+
+def test_ab2cn_byte_model_at_2048_dynamic_leith():
+    """One explicit evaluation per step: 38 mixed arrays, 13 spectra and the two factor fields (Eq. 4)."""
+    wl = S.island2048_dleith()
+    n, K = wl.n, (wl.n - 1) // 3
+    I, Sp, R = n * (K + 1) * 8, (K + 1) * (2 * K + 1) * 8, n * n * 4
+    model = bench.algorithmic_bytes_ab2cn(wl, True)
+    assert sum(a * b for a, b in model.values()) == 38 * I + 13 * Sp + 2 * R
+    assert all(a == 1 for a, _ in model.values())
+
+
+def test_series_pair_count_matches_the_oracle_nan_pattern():
+    import numpy as np
+    import oracle as O
+    les = np.zeros((5, 2))
+    ff = np.zeros((7, 2))
+    dist, _ = O.lag_table(les, ff, -3, 4)
+    assert bench.valid_pairs(5, 7, -3, 4) == int(np.sum(~np.isnan(dist)))
