@@ -420,7 +420,182 @@ def run_series_bench(args):
         dist.destroy_process_group()
 
 
-TOOLS = {"series512": {"ours": run_series_bench, "reference": run_series_reference}}
+# ---------------------------------------------------------------------------
+# Ensemble: 96 independent FP32 members (24 each of 256^2, 384^2, 512^2,
+# 768^2; island / cape; the four closures; random beta, U), one CUDA graph
+# per ensemble step with the members as parallel branches.
+# ---------------------------------------------------------------------------
+ENS_METRIC = "grid-pt-steps/s (sum of N_i^2) of a 96-member FP32 LES ensemble, 256^2-768^2, 4 closures"
+
+
+def time_ensemble_oracle(wls, max_seconds: float):
+    """The oracle stepping the first eight members (two of each size) in turn, bounded wall time."""
+    import oracle as O
+    refs = []
+    for w in wls[:8]:
+        ref = O.QGOracle(w.n, w.L, w.beta, w.U, w.mask(), w.sponge_field(), O.Closure(w.closure, c=w.c),
+                         O.Params(dt=w.dt, nu=w.nu, mu=w.mu, eta=w.eta, sponge_rate=w.sponge_rate))
+        ref.set_state(w.omega0())
+        refs.append((ref, w.n * w.n))
+    done = 0
+    pts = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < max_seconds:
+        ref, n2 = refs[done % len(refs)]
+        ref.step(1)
+        done += 1
+        pts += n2
+    return done, pts, time.perf_counter() - t0
+
+
+def run_ensemble_reference(args, budget):
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    wls = S.ensemble96()
+    done, pts, el = time_ensemble_oracle(wls, budget)
+    value = pts / el
+    line = {
+        "metric": ENS_METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": 1e3 * el, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": "ensemble96", "members": len(wls)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} member-steps (256^2-768^2) of the FP64 numpy oracle, {el:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ensemble_bench(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2508_06678_gb300 as qg
+    from paper_2508_06678_gb300._lib import LIB_PATH, load
+    if not os.path.exists(LIB_PATH):
+        from paper_2508_06678_gb300.build import build
+        build()
+    load()
+    wls = S.ensemble96()
+    pts = sum(w.n * w.n for w in wls)
+    stream = torch.cuda.Stream()
+    ens = qg.QGEnsemble.from_workloads(wls, precision=qg.QG_FP32, stream=stream)
+    w0 = [w.omega0() for w in wls]
+    for m, w in zip(ens.members, w0):
+        m.set_state(w)
+    ens.step(args.warmup)
+    ens.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except (AttributeError, RuntimeError):
+        gpu_id = str(local)
+    launches0 = sum(m_launches(m) for m in ens.members)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ens.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ens.sync()
+    launches = sum(m_launches(m) for m in ens.members) - launches0
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    value = world * pts / (ms / 1e3)
+
+    # the same members stepped one after another (each replaying its own step graph) on one stream
+    solo = [qg.QGSolver.from_workload(w, precision=qg.QG_FP32, stream=stream) for w in wls]
+    for s_, w in zip(solo, w0):
+        s_.set_state(w)
+        s_.step(3)
+    torch.cuda.synchronize()
+    k_seq = max(1, args.steps // 4)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k_seq):
+        for s_ in solo:
+            s_.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / k_seq
+    for s_ in solo:
+        s_.close()
+
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    step_bytes = sum(sum(a * b for a, b in algorithmic_bytes(w, True).values()) for w in wls)
+    achieved = step_bytes / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "ensemble step (every member's kernels, concurrent graph branches)",
+                "peak_source": peak_src, "bytes_per_launch": step_bytes, "avg_launch_us": ms * 1e3,
+                "measured_in": "CUDA events around the K replayed ensemble steps"}
+
+    # end to end: host states in, K steps, host states and diagnostics out
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m, w in zip(ens.members, w0):
+        m.set_state(w.astype(np.float32))
+    ens.step(args.steps)
+    outs = [m.get_state(dtype=np.float32) for m in ens.members]
+    diag = [m.diagnostics() for m in ens.members]
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    nbytes = sum(w.n * w.n * 4 for w in wls)
+    e2e = {"value": world * pts * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
+           "d2h_bytes_per_step": (nbytes + 56 * len(wls)) / args.steps,
+           "api": "per member qg_set_state(host) + qg_ensemble_step(K) + per member qg_get_state(host), "
+                  "qg_diagnostics"}
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            done, cpts, el = time_ensemble_oracle(wls, args.cpu_seconds)
+            cpu = {"value": cpts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{done} member-steps (256^2-768^2) of the FP64 numpy oracle, {el:.1f} s"}
+        line = {
+            "metric": ENS_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble96", "members": len(wls), "sizes": "24 x (256, 384, 512, 768)^2",
+                       "sum_n2": pts, "closures": "smag, leith, dyn-smag, dyn-leith", "scheme": "rk3",
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "working set ~1 GB > 126 MB L2 (no flush)",
+                       "sequential_ms_per_step": seq_ms, "concurrency_speedup": seq_ms / ms,
+                       "all_finite": all(d["finite"] for d in diag)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def m_launches(m) -> int:
+    """Kernel launches of one solver handle so far (every kernel class)."""
+    import ctypes as C
+    from paper_2508_06678_gb300._lib import load
+    counts = (C.c_int32 * 8)()
+    load().qg_kernel_times(m.h, counts, None, 8)
+    return int(sum(counts))
+
+
+TOOLS = {"series512": {"ours": run_series_bench, "reference": run_series_reference},
+         "ensemble96": {"ours": run_ensemble_bench, "reference": run_ensemble_reference}}
 
 
 def main():

@@ -213,6 +213,51 @@ int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32
                       int32_t dtype, int32_t on_device, int32_t lag_min, int32_t lag_max, void* stream, double* dist,
                       double* pcc, double* mean_dist, int32_t* phase, double* kernel_ms);
 
+/* Ensembles of independent members (Sec. IV runs many LES of different
+ * grids, closures and parameters; the paper gives no batching, this is the
+ * batched form of qg_step).  Each member is a full qg_handle on a stream of
+ * its own; a step of the ensemble advances every member by one step of its
+ * own scheme.  After one eager step it is replayed as one CUDA graph in which
+ * the members' steps are parallel branches between a fork and a join on the
+ * ensemble's stream, so members' kernels run side by side on the GPU.  A
+ * member's results are bitwise those of the same member stepped alone. */
+typedef struct qg_ensemble qg_ensemble;
+
+typedef struct {
+  qg_grid grid;
+  qg_closure closure;
+  qg_params params;
+  double beta;
+  double U;
+  const double* mask;   /* chi_obs, n*n host doubles, or NULL */
+  const double* sponge; /* chi_sponge, n*n host doubles, or NULL */
+} qg_member;            /* 120 bytes */
+
+/* Create count >= 1 members as qg_create would (host masks copied; on error
+ * nothing is left allocated and the message names the member).  stream: the
+ * ensemble's cudaStream_t (capturable, i.e. not the legacy default stream),
+ * or NULL to let the ensemble create one. */
+int qg_ensemble_create(const qg_member* members, int32_t count, void* stream, qg_ensemble** out);
+
+/* Borrow member i's handle for qg_set_state, qg_get_state, qg_diagnostics,
+ * qg_profile, qg_kernel_times (valid until qg_ensemble_destroy; do not
+ * qg_destroy it).  Work queued on it is ordered before the next ensemble step
+ * and after the previous one. */
+int qg_ensemble_handle(qg_ensemble* e, int32_t i, qg_handle** out);
+
+/* Enqueue nsteps >= 0 steps of every member (asynchronous).  A member whose
+ * state became non-finite stops computing (its kernels return at once); the
+ * others go on. */
+int qg_ensemble_step(qg_ensemble* e, int32_t nsteps);
+
+/* Wait for all members; QG_ERR_NONFINITE (or QG_ERR_TIMEOUT) from the first
+ * member that reports it, whose index goes to *first_bad (-1 if none; may be
+ * NULL). */
+int qg_ensemble_sync(qg_ensemble* e, int32_t* first_bad);
+
+/* Destroy every member and the ensemble's own streams (NULL is ignored). */
+void qg_ensemble_destroy(qg_ensemble* e);
+
 /* Kernel classes reported by qg_kernel_times. */
 #define QG_K_ROW_STAGE 0   /* row pass of an RK stage (products of Eq. 1, 9-14) */
 #define QG_K_COL_REDUCE 1  /* column pass: Germano partial sums (Eq. 12, 14) */

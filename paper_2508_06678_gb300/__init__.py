@@ -6,11 +6,11 @@ every step of the computation runs in libqg's CUDA kernels.
 from ._lib import (QG_DLEITH, QG_DSMAG, QG_ERR_ARG, QG_ERR_CUDA, QG_ERR_NONFINITE, QG_ERR_OOM, QG_ERR_UNSUPPORTED,
                    QG_FP32, QG_FP64, QG_LEITH, QG_NONE, QG_OK, QG_SCHEME_AB2CN, QG_SCHEME_RK3_EXACT, QG_SMAG,
                    QGError, load)
-from .qg import (QGSolver, qg_create, qg_destroy, qg_diagnostics, qg_get_state, qg_grid_filter, qg_last_error,
+from .qg import (QGEnsemble, QGSolver, qg_create, qg_destroy, qg_diagnostics, qg_get_state, qg_grid_filter, qg_last_error,
                  qg_series_compare, qg_set_state, qg_sgs_apriori, qg_step, qg_sync, qg_version)
 
 __all__ = [
-    "QGSolver", "QGError", "load", "qg_create", "qg_destroy", "qg_diagnostics", "qg_get_state", "qg_set_state",
+    "QGSolver", "QGEnsemble", "QGError", "load", "qg_create", "qg_destroy", "qg_diagnostics", "qg_get_state", "qg_set_state",
     "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_step", "qg_sync", "qg_last_error", "qg_version",
     "QG_NONE", "QG_SMAG", "QG_LEITH", "QG_DSMAG", "QG_DLEITH", "QG_FP32", "QG_FP64",
     "QG_SCHEME_RK3_EXACT", "QG_SCHEME_AB2CN",

@@ -50,6 +50,11 @@ class qg_diag(C.Structure):
                 ("max_abs_omega", C.c_double), ("step", C.c_int64), ("finite", C.c_int32), ("reserved", C.c_int32)]
 
 
+class qg_member(C.Structure):
+    _fields_ = [("grid", qg_grid), ("closure", qg_closure), ("params", qg_params), ("beta", C.c_double),
+                ("U", C.c_double), ("mask", C.POINTER(C.c_double)), ("sponge", C.POINTER(C.c_double))]
+
+
 DP = C.POINTER(C.c_double)
 
 # name -> (restype, argtypes): every symbol include/qg.h declares
@@ -67,6 +72,11 @@ SIGNATURES = {
     "qg_grid_filter": (C.c_int, [DP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, DP]),
     "qg_series_compare": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_void_p, DP, DP, DP, C.POINTER(C.c_int32), DP]),
+    "qg_ensemble_create": (C.c_int, [C.POINTER(qg_member), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "qg_ensemble_handle": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "qg_ensemble_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "qg_ensemble_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "qg_ensemble_destroy": (None, [C.c_void_p]),
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int32]),
     "qg_field_stats_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),

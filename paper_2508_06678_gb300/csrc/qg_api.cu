@@ -20,7 +20,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
+#include <array>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -694,6 +696,96 @@ int state_to_phys(qg_handle* h) {
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// Ensembles of independent members (different grids, closures, parameters).
+// Each member is a full handle on a stream of its own.  A step of the
+// ensemble is one CUDA graph in which the members' steps are parallel
+// branches between a fork and a join on the ensemble's stream, so the GPU
+// runs the members' kernels side by side: a single 256^2 - 768^2 member
+// leaves most of the 152 SMs idle between its launches.
+// ---------------------------------------------------------------------------
+struct qg_ensemble {
+  std::vector<qg_handle*> h;
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> ev;  // per member: tail of its stream before a step, its branch's end inside one
+  std::vector<std::array<int32_t, QG_NUM_KCLASS>> graph_launches;
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+  int64_t eager_steps = 0;
+  ~qg_ensemble() {
+    if (main) cudaStreamSynchronize(main);
+    if (exec) cudaGraphExecDestroy(exec);
+    for (qg_handle* x : h) qg_destroy(x);
+    for (cudaStream_t s : st) cudaStreamDestroy(s);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (done) cudaEventDestroy(done);
+    if (own_main && main) cudaStreamDestroy(main);
+  }
+};
+
+namespace {
+
+// fork on the ensemble stream, one step of every member on its stream, join
+int ens_enqueue(qg_ensemble* e) {
+  CK(cudaEventRecord(e->fork, e->main), "ensemble: fork");
+  for (size_t i = 0; i < e->h.size(); ++i) {
+    CK(cudaStreamWaitEvent(e->st[i], e->fork, 0), "ensemble: fork wait");
+    const int rc = enqueue_any_step(e->h[i]);
+    if (rc) return rc;
+    CK(cudaEventRecord(e->ev[i], e->st[i]), "ensemble: join");
+    CK(cudaStreamWaitEvent(e->main, e->ev[i], 0), "ensemble: join wait");
+  }
+  return QG_OK;
+}
+
+void ens_build_graph(qg_ensemble* e) {
+  e->graph_tried = true;
+  if (getenv("QG_NO_GRAPH")) return;
+  const size_t m = e->h.size();
+  std::vector<std::array<int32_t, QG_NUM_KCLASS>> saved(m);
+  std::vector<int64_t> step(m);
+  std::vector<double> t(m);
+  std::vector<char> hist(m);
+  for (size_t i = 0; i < m; ++i) {
+    memcpy(saved[i].data(), e->h[i]->launches, sizeof(e->h[i]->launches));
+    step[i] = e->h[i]->step;
+    t[i] = e->h[i]->t;
+    hist[i] = e->h[i]->ab2_hist;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int rc = ens_enqueue(e);
+  const cudaError_t err = cudaStreamEndCapture(e->main, &g);
+  e->graph_launches.assign(m, {});
+  for (size_t i = 0; i < m; ++i) {
+    qg_handle* x = e->h[i];
+    for (int c = 0; c < QG_NUM_KCLASS; ++c) e->graph_launches[i][c] = x->launches[c] - saved[i][c];
+    memcpy(x->launches, saved[i].data(), sizeof(x->launches));
+    x->step = step[i];
+    x->t = t[i];
+    x->ab2_hist = hist[i];
+  }
+  if (rc != QG_OK || err != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) e->exec = ex;
+  cudaGraphDestroy(g);
+  cudaGetLastError();
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* qg_last_error(void) { return g_err.c_str(); }
@@ -1120,5 +1212,118 @@ int qg_kernel_times(qg_handle* h, int32_t* counts, double* ms, int32_t nclass) {
   }
   return QG_OK;
 }
+
+
+int qg_ensemble_create(const qg_member* members, int32_t count, void* cuda_stream, qg_ensemble** out) {
+  if (!members || !out || count < 1) return fail(QG_ERR_ARG, "qg_ensemble_create: NULL argument or count < 1");
+  *out = nullptr;
+  auto* e = new (std::nothrow) qg_ensemble();
+  if (!e) return fail(QG_ERR_OOM, "qg_ensemble_create: out of host memory");
+  e->main = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t ce = cudaSuccess;
+  if (!e->main) {
+    ce = cudaStreamCreateWithFlags(&e->main, cudaStreamNonBlocking);
+    e->own_main = ce == cudaSuccess;
+  }
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    if (!e->own_main) e->main = nullptr;
+    delete e;
+    return cuda_fail(ce, "qg_ensemble_create: stream/event");
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) e->st.push_back(s);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (ce == cudaSuccess) e->ev.push_back(ev);
+    if (ce != cudaSuccess) {
+      delete e;
+      return cuda_fail(ce, "qg_ensemble_create: member stream");
+    }
+    const qg_member& m = members[i];
+    qg_handle* x = nullptr;
+    const int rc = qg_create(&m.grid, m.beta, m.U, m.mask, m.sponge, &m.closure, &m.params, s, &x);
+    if (rc != QG_OK) {
+      const std::string why = g_err;
+      delete e;
+      return fail(rc, "qg_ensemble_create: member %d: %s", (int)i, why.c_str());
+    }
+    e->h.push_back(x);
+  }
+  *out = e;
+  return QG_OK;
+}
+
+int qg_ensemble_handle(qg_ensemble* e, int32_t i, qg_handle** out) {
+  if (!e || !out || i < 0 || (size_t)i >= e->h.size()) return fail(QG_ERR_ARG, "qg_ensemble_handle: bad argument");
+  *out = e->h[i];
+  return QG_OK;
+}
+
+int qg_ensemble_step(qg_ensemble* e, int32_t nsteps) {
+  if (!e) return fail(QG_ERR_ARG, "qg_ensemble_step: NULL ensemble");
+  if (nsteps < 0) return fail(QG_ERR_ARG, "qg_ensemble_step: nsteps < 0");
+  if (nsteps == 0) return QG_OK;
+  const size_t m = e->h.size();
+  // work already queued on a member's stream (set_state, ...) precedes the step
+  for (size_t i = 0; i < m; ++i) {
+    CK(cudaEventRecord(e->ev[i], e->st[i]), "qg_ensemble_step: member tail");
+    CK(cudaStreamWaitEvent(e->main, e->ev[i], 0), "qg_ensemble_step: member tail wait");
+  }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    bool eager = false;  // the Euler start of the paper's scheme and tracing run eagerly
+    for (qg_handle* x : e->h) eager = eager || x->prof || (x->scheme == QG_SCHEME_AB2CN && !x->ab2_hist);
+    if (!eager && e->eager_steps > 0 && !e->graph_tried) ens_build_graph(e);
+    if (!eager && e->exec) {
+      CK(cudaGraphLaunch(e->exec, e->main), "qg_ensemble_step: graph launch");
+      for (size_t i = 0; i < m; ++i) {
+        qg_handle* x = e->h[i];
+        for (int c = 0; c < QG_NUM_KCLASS; ++c) x->launches[c] += e->graph_launches[i][c];
+        x->step += 1;
+        x->t += x->par.dt;
+        if (x->scheme == QG_SCHEME_AB2CN) x->ab2_hist = true;
+      }
+    } else {
+      const int rc = ens_enqueue(e);
+      if (rc) return rc;
+      e->eager_steps += 1;
+    }
+  }
+  // later work on a member's stream follows the step; each member's status flag comes back
+  CK(cudaEventRecord(e->done, e->main), "qg_ensemble_step: done");
+  for (size_t i = 0; i < m; ++i) {
+    qg_handle* x = e->h[i];
+    CK(cudaStreamWaitEvent(e->st[i], e->done, 0), "qg_ensemble_step: done wait");
+    CK(cudaMemcpyAsync(x->flag_host, x->flag, sizeof(int), cudaMemcpyDeviceToHost, x->stream),
+       "qg_ensemble_step: flag");
+    CK(cudaEventRecord(x->flag_event, x->stream), "qg_ensemble_step: flag event");
+    x->flag_pending = true;
+  }
+  return QG_OK;
+}
+
+int qg_ensemble_sync(qg_ensemble* e, int32_t* first_bad) {
+  if (!e) return fail(QG_ERR_ARG, "qg_ensemble_sync: NULL ensemble");
+  if (first_bad) *first_bad = -1;
+  CK(cudaStreamSynchronize(e->main), "qg_ensemble_sync");
+  int status = QG_OK;
+  for (size_t i = 0; i < e->h.size(); ++i) {
+    const int rc = qg_sync(e->h[i]);
+    if (rc != QG_OK && status == QG_OK) {
+      status = rc;
+      if (first_bad) *first_bad = (int32_t)i;
+    }
+  }
+  if (status != QG_OK) {
+    const std::string why = g_err;
+    return fail(status, "qg_ensemble_sync: member %d: %s", first_bad ? *first_bad : -1, why.c_str());
+  }
+  return QG_OK;
+}
+
+void qg_ensemble_destroy(qg_ensemble* e) { delete e; }
 
 }  // extern "C"

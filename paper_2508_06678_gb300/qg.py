@@ -13,10 +13,11 @@ from dataclasses import dataclass
 import numpy as np
 
 from ._lib import (QG_ERR_NONFINITE, QG_FP32, QG_FP64, QG_OK, QGError, check, load, qg_closure, qg_diag, qg_grid,
-                   qg_params)
+                   qg_member, qg_params)
 
 __all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_step", "qg_sync", "qg_diagnostics", "qg_destroy",
-           "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_last_error", "qg_version", "QGSolver"]
+           "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_last_error", "qg_version", "QGSolver",
+           "QGEnsemble"]
 
 
 def _dptr(a):
@@ -240,10 +241,100 @@ class QGSolver:
     def diagnostics(self, raise_nonfinite: bool = True) -> dict:
         return qg_diagnostics(self.h, raise_nonfinite)
 
+    @classmethod
+    def _borrow(cls, h: int, n: int, L: float, precision: int) -> "QGSolver":
+        """A view of a handle owned elsewhere (an ensemble member): close() leaves it alone."""
+        obj = cls.__new__(cls)
+        obj.cfg = _Cfg(n, L, precision)
+        obj.h = h
+        obj._owned = False
+        return obj
+
     def close(self) -> None:
-        if self.h:
+        if self.h and getattr(self, "_owned", True):
             qg_destroy(self.h)
-            self.h = 0
+        self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _member_args(n, *, L=2 * math.pi, precision=QG_FP64, beta=0.0, U=0.0, mask=None, sponge=None, kind=0, c=0.0,
+                 test_ratio=2.0, dt=2e-3, nu=1.0 / 200.0, mu=0.0, eta=1e-3, sponge_rate=50.0, scheme=0):
+    return dict(n=n, L=L, precision=precision, beta=beta, U=U, mask=mask, sponge=sponge, kind=kind, c=c,
+                test_ratio=test_ratio, dt=dt, nu=nu, mu=mu, eta=eta, sponge_rate=sponge_rate, scheme=scheme)
+
+
+class QGEnsemble:
+    """Owning wrapper of a libqg ensemble.  ``members[i]`` is a borrowed QGSolver view of member i.
+
+    Each entry of ``specs`` holds QGSolver's keyword arguments plus ``n``.
+    """
+
+    def __init__(self, specs, stream=None):
+        self.e = 0
+        args = [_member_args(**sp) for sp in specs]
+        arr = (qg_member * len(args))()
+        keep = []
+        for i, a in enumerate(args):
+            n = a["n"]
+            m = arr[i]
+            m.grid = qg_grid(n, a["precision"], a["L"])
+            m.closure = qg_closure(a["kind"], 0, a["c"], a["test_ratio"])
+            m.params = qg_params(a["dt"], a["nu"], a["mu"], a["eta"], a["sponge_rate"], a["scheme"], 0)
+            m.beta = a["beta"]
+            m.U = a["U"]
+            for name in ("mask", "sponge"):
+                d = _dptr(a[name])
+                if d is not None:
+                    if d[0].size != n * n:
+                        raise ValueError(f"member {i}: {name} must hold n*n values")
+                    keep.append(d[0])
+                    setattr(m, name, d[1])
+        out = C.c_void_p()
+        check(load().qg_ensemble_create(arr, len(args), _stream_ptr(stream), C.byref(out)), "qg_ensemble_create")
+        self.e = out.value
+        self.members = []
+        for i, a in enumerate(args):
+            h = C.c_void_p()
+            check(load().qg_ensemble_handle(self.e, i, C.byref(h)), "qg_ensemble_handle")
+            self.members.append(QGSolver._borrow(h.value, a["n"], a["L"], a["precision"]))
+
+    @classmethod
+    def from_workloads(cls, wls, precision: int = QG_FP32, scheme: int = 0, stream=None) -> "QGEnsemble":
+        return cls([dict(n=w.n, L=w.L, precision=precision, beta=w.beta, U=w.U, mask=w.mask(),
+                         sponge=w.sponge_field(), kind=w.closure, c=w.c, test_ratio=w.test_ratio, dt=w.dt, nu=w.nu,
+                         mu=w.mu, eta=w.eta, sponge_rate=w.sponge_rate, scheme=scheme) for w in wls], stream)
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, nsteps: int = 1) -> None:
+        check(load().qg_ensemble_step(self.e, int(nsteps)), "qg_ensemble_step")
+
+    def sync(self) -> None:
+        bad = C.c_int32(-1)
+        rc = load().qg_ensemble_sync(self.e, C.byref(bad))
+        if rc != QG_OK:
+            err = QGError(rc, "qg_ensemble_sync", load().qg_last_error().decode())
+            err.member = bad.value
+            raise err
+
+    def close(self) -> None:
+        for m in getattr(self, "members", []):
+            m.h = 0
+        if self.e:
+            load().qg_ensemble_destroy(self.e)
+            self.e = 0
 
     def __del__(self):
         try:

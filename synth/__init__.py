@@ -202,6 +202,23 @@ def island2048_dleith() -> Workload:
     return Workload("island2048-dleith", 2048, "island", beta=5.0, U=0.5, closure=DLEITH, radius=0.2, seed=0, steps=5000)
 
 
+def ensemble96(seed: int = 7) -> list:
+    """96 independent LES members: 24 each of 256^2, 384^2, 512^2 and 768^2; island and cape geometries; the four
+    closures; beta ~ U[2, 12) and U ~ U[0.3, 1.0) from SplitMix64(seed); member i starts from init_field(100 + i)."""
+    sizes = [256, 384, 512, 768]
+    kinds = [SMAG, LEITH, DSMAG, DLEITH]
+    u = uniform01(seed, 2 * 96)
+    out = []
+    for i in range(96):
+        n = sizes[i % 4]
+        kind = kinds[(i // 4) % 4]
+        geometry = "island" if (i // 16) % 2 == 0 else "cape"
+        c = {SMAG: 0.17, LEITH: 0.25}.get(kind, 0.0)
+        out.append(Workload(f"ens{i:02d}-{geometry}{n}-{CLOSURE_NAMES[kind]}", n, geometry, beta=2.0 + 10.0 * u[2 * i],
+                            U=0.3 + 0.7 * u[2 * i + 1], closure=kind, c=c, seed=100 + i, steps=1000))
+    return out
+
+
 def wave_series(seed: int, n: int, nsnap: int, L: float = 2 * math.pi, speed=(0.5, 0.25), t0: float = 0.0,
                 dt_snap: float = 1.0, nmodes: int = 6, noise: float = 0.0, noise_seed: int | None = None) -> np.ndarray:
     """A seeded snapshot series of a pattern translating at a uniform speed.

@@ -65,3 +65,9 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_member_struct_layout(lib):
+    import ctypes as C
+    from paper_2508_06678_gb300._lib import qg_member
+    assert C.sizeof(qg_member) == 120
