@@ -12,3 +12,4 @@ the function.  Parity status per function is stated in ``qg.__doc__`` and
 """
 from .qg import *  # noqa: F401,F403
 from .apost import *  # noqa: F401,F403
+from .adjoint import *  # noqa: F401,F403
