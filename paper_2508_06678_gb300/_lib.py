@@ -77,6 +77,7 @@ SIGNATURES = {
     "qg_ensemble_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_ensemble_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "qg_ensemble_destroy": (None, [C.c_void_p]),
+    "qg_step_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, DP]),
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int32]),
     "qg_field_stats_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),

@@ -20,9 +20,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <array>
+#include <utility>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -199,6 +201,10 @@ struct qg_handle {
   bool ab2_hist = false;
   void* fac_b = nullptr;
   void* fac_s = nullptr;
+  void* chi_s = nullptr;  // the sponge mask itself (the adjoint's sponge-rate derivative)
+  // workspace of qg_step_vjp, allocated by its first call: spectral, physical and mixed arrays, dot results
+  std::vector<void*> adj_S, adj_P, adj_M;
+  double* adj_dots = nullptr;
   void* tw = nullptr;
   void* ptw = nullptr;  // per-pass twiddle table of the power-of-two kernels
   void* visc_x = nullptr;
@@ -675,6 +681,294 @@ int enqueue_step_ab2(qg_handle* h) {
 
 int enqueue_any_step(qg_handle* h) { return h->scheme == QG_SCHEME_AB2CN ? enqueue_step_ab2(h) : enqueue_step(h); }
 
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the RK3 step (qg_step_vjp).  The step's forward stages
+// are recomputed from w_n with unfused operations (transform passes, the
+// adjoint module's pointwise and multiplier kernels), then the transposes run
+// in reverse order: final projection, sponge, Brinkman, viscous factor, the
+// three Shu-Osher stages.  Each stage's transpose linearises L at that stage's
+// state: conjugate multipliers for the spectral operators, pointwise products
+// for the nonlinear terms (Eq. 1, 9, 10, 13).
+// ---------------------------------------------------------------------------
+constexpr int kAdjNS = 19;  // spectral: w0..w3, w5, lam, lam', acc, 11 product / SGS spectra
+constexpr int kAdjNP = 19;  // physical: 6 forward fields, 3 adjoint fields, 8 products, input, output
+constexpr int kAdjNM = 6;   // mixed: the outputs of one derive pass
+
+int adj_alloc(qg_handle* h) {
+  if (!h->adj_S.empty()) return QG_OK;
+  const size_t csz = 2 * h->esz;
+  const size_t spec_bytes = (size_t)h->g.Kcp * h->g.SP * csz;
+  const size_t mixed_bytes = (size_t)h->g.n * h->g.IP * csz;
+  const size_t phys_bytes = (size_t)h->g.n * h->g.n * h->esz;
+  std::vector<void*> S(kAdjNS), P(kAdjNP), M(kAdjNM);
+  int rc = QG_OK;
+  for (auto& p : S) if (!rc) rc = dalloc(h, &p, spec_bytes);
+  for (auto& p : P) if (!rc) rc = dalloc(h, &p, phys_bytes);
+  for (auto& p : M) if (!rc) rc = dalloc(h, &p, mixed_bytes);
+  void* dots = nullptr;
+  if (!rc) rc = dalloc(h, &dots, sizeof(double) * (kAdjDotBlocks + 8));
+  if (!rc && h->fast) {
+    const int BR = h->g.n < 256 ? h->g.n : 256;
+    for (void* m : M) if (!rc) rc = add_tensor_map(h, m, h->W, BR);
+  }
+  if (rc) return rc;
+  h->adj_S = S;
+  h->adj_P = P;
+  h->adj_M = M;
+  h->adj_dots = static_cast<double*>(dots);
+  return QG_OK;
+}
+
+// spectral band (T F[f], mean removed if asked) of a physical field
+int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
+  RowDesc r{};
+  r.prog = RP_COPY;
+  r.nin = 1;
+  r.nout = 1;
+  r.in_phys = 1;
+  r.phys_in = P;
+  r.out[0] = h->adj_M[0];
+  int rc = run_row(h, r, QG_K_OTHER, false);
+  if (rc) return rc;
+  ColDesc c = col_base(h);
+  c.op = CO_FORWARD;
+  c.nfwd = 1;
+  c.fin[0] = h->adj_M[0];
+  c.w0 = S;
+  c.store_w0 = 1;
+  c.zero_mean = zero_mean ? 1 : 0;
+  c.nder = 0;
+  return run_col(h, c, QG_K_OTHER, false);
+}
+
+// physical fields of derived spectra (codes D_W, D_U (with U), D_V, D_WX, D_WY, D_PXY, D_PD) of a spectral state
+int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, std::initializer_list<void*> P) {
+  ColDesc c = col_base(h);
+  c.op = CO_DERIVE;
+  c.w0 = const_cast<void*>(S);
+  c.nder = 0;
+  for (int code : codes) {
+    c.der[c.nder] = code;
+    c.dout[c.nder] = h->adj_M[c.nder];
+    ++c.nder;
+  }
+  int rc = run_col(h, c, QG_K_OTHER, false);
+  int i = 0;
+  for (void* dst : P) {
+    if (rc) return rc;
+    RowDesc r{};
+    r.prog = RP_COPY;
+    r.nin = 1;
+    r.nout = 1;
+    r.in[0] = h->adj_M[i++];
+    r.out_phys = 1;
+    r.phys_out = dst;
+    rc = run_row(h, r, QG_K_OTHER, false);
+  }
+  return rc;
+}
+
+int adj_combine(qg_handle* h, void* out, bool accumulate, bool zero_mean,
+                std::initializer_list<AdjTerm> terms) {
+  AdjCombine a{};
+  a.out = out;
+  a.accumulate = accumulate;
+  a.zero_mean = zero_mean;
+  for (const AdjTerm& t : terms) a.term[a.nterm++] = t;
+  a.nu = h->par.nu;
+  a.mu = h->par.mu;
+  a.dt = h->par.dt;
+  CK(h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream),
+     "adjoint: combine");
+  return QG_OK;
+}
+
+int adj_products(qg_handle* h, AdjProducts a) {
+  const size_t count = (size_t)h->g.n * h->g.n;
+  CK(h->fp32 ? launch_adj_products<float>(count, a, h->stream) : launch_adj_products<double>(count, a, h->stream),
+     "adjoint: products");
+  return QG_OK;
+}
+
+int adj_scale(qg_handle* h, const void* f, const void* x0, double s0, void* out0, const void* x1, double s1,
+              void* out1) {
+  const size_t count = (size_t)h->g.n * h->g.n;
+  CK(h->fp32 ? launch_adj_scale<float>(count, f, x0, s0, out0, x1, s1, out1, h->stream)
+             : launch_adj_scale<double>(count, f, x0, s0, out0, x1, s1, out1, h->stream),
+     "adjoint: scale");
+  return QG_OK;
+}
+
+// the forward products of a stage state's spectral fields: J, and g w_x, g w_y with a closure
+int adj_stage_fields(qg_handle* h, const void* Sw, int kind) {
+  auto& P = h->adj_P;
+  if (kind == AK_SMAG)
+    return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY, D_PXY, D_PD}, {P[0], P[1], P[2], P[3], P[4], P[5]});
+  return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY}, {P[0], P[1], P[2], P[3]});
+}
+
+AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode) {
+  auto& P = h->adj_P;
+  AdjProducts a{};
+  a.kind = kind;
+  a.mode = mode;
+  a.u = P[0];
+  a.v = P[1];
+  a.wx = P[2];
+  a.wy = P[3];
+  a.pxy = P[4];
+  a.pd = P[5];
+  a.lam = P[6];
+  a.lx = P[7];
+  a.ly = P[8];
+  for (int k = 0; k < 8; ++k) a.out[k] = P[9 + k];
+  return a;
+}
+
+// L(w) = -J - beta psi_x + C div(g grad w) of the stage state Sw into spectral Sout scaled as
+// Sout = a w0 + b (ws + dt L(ws)) (Shu-Osher stage); spectra S[8..10] are scratch
+int adj_forward_stage(qg_handle* h, int kind, double C, const void* S0, const void* Sw, void* Sout, double a,
+                      double b) {
+  auto& S = h->adj_S;
+  auto& P = h->adj_P;
+  const double dt = h->par.dt;
+  int rc = adj_stage_fields(h, Sw, kind);
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD));
+  if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
+  if (kind != AK_NONE) {
+    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
+    if (!rc) rc = adj_to_spec(h, P[11], S[10], false);
+  }
+  if (rc) return rc;
+  if (kind == AK_NONE)
+    return adj_combine(h, Sout, false, false,
+                       {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta}});
+  return adj_combine(h, Sout, false, false,
+                     {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta},
+                      {S[9], AM_IX, b * dt * C}, {S[10], AM_IY, b * dt * C}});
+}
+
+// Slam_out = b lam + L'(ws)^T (b dt lam) (one Shu-Osher stage in reverse); the derivative in C,
+// b dt sum(lam * div(g grad ws)), goes to adj_dots[slot]
+int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Sw, const void* Slam, void* Slam_out, double b,
+                      int slot) {
+  auto& S = h->adj_S;
+  auto& P = h->adj_P;
+  const double dt = h->par.dt, bd = b * dt;
+  int rc = adj_stage_fields(h, Sw, kind);
+  if (!rc) rc = adj_to_phys(h, Slam, {D_W, D_WX, D_WY}, {P[6], P[7], P[8]});
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT));
+  const int nprod = kind == AK_NONE ? 4 : (kind == AK_LEITH ? 6 : 8);
+  for (int k = 0; k < nprod && !rc; ++k) rc = adj_to_spec(h, P[9 + k], S[8 + k], false);
+  if (rc) return rc;
+  AdjCombine a{};
+  a.out = Slam_out;
+  a.nu = h->par.nu;
+  a.mu = h->par.mu;
+  a.dt = dt;
+  auto add = [&](const void* in, int code, double coef) { a.term[a.nterm++] = AdjTerm{in, code, coef}; };
+  add(Slam, AM_ONE, b);
+  // -J: each factor's transpose takes the other factor
+  add(S[8], AM_CU, -bd);
+  add(S[9], AM_CV, -bd);
+  add(S[10], AM_CX, -bd);
+  add(S[11], AM_CY, -bd);
+  // -beta psi_x = (i beta k_x / |k|^2) w: transpose -i beta k_x / |k|^2
+  add(Slam, AM_CV, -bd * h->beta);
+  if (kind != AK_NONE) {
+    add(S[12], AM_CX, bd * C);
+    add(S[13], AM_CY, bd * C);
+    if (kind == AK_SMAG) {
+      add(S[14], AM_XY, bd * C);
+      add(S[15], AM_DD, bd * C);
+    }
+  }
+  CK(h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream),
+     "adjoint: stage combine");
+  if (kind != AK_NONE) {
+    // derivative in C: sum over points of lam * T div(g grad ws) (Parseval over the band)
+    rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD));
+    if (!rc) rc = adj_to_spec(h, P[10], S[16], false);
+    if (!rc) rc = adj_to_spec(h, P[11], S[17], false);
+    if (!rc) rc = adj_combine(h, S[18], false, false, {{S[16], AM_IX, 1.0}, {S[17], AM_IY, 1.0}});
+    if (rc) return rc;
+    const double n2 = double(h->g.n) * double(h->g.n);
+    CK(h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots, h->adj_dots + kAdjDotBlocks + slot,
+                                            h->stream)
+               : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
+                                             h->adj_dots + kAdjDotBlocks + slot, h->stream),
+       "adjoint: C derivative");
+  }
+  return QG_OK;
+}
+
+// in: physical w_n and lam_{n+1} in the working precision (P[17], P[18]); out: lam_n in P[18];
+// adj_dots[kAdjDotBlocks + 0..2] = the stages' C derivatives, [+3] = the sponge-rate derivative
+int adj_step(qg_handle* h) {
+  auto& S = h->adj_S;
+  auto& P = h->adj_P;
+  const int kind = h->cl.kind == QG_SMAG ? AK_SMAG : h->cl.kind == QG_LEITH ? AK_LEITH : AK_NONE;
+  const double C = kind == AK_NONE ? 0.0 : h->static_coeff;
+  const double dt = h->par.dt;
+  double* dots = h->adj_dots + kAdjDotBlocks;
+  CK(cudaMemsetAsync(dots, 0, 8 * sizeof(double), h->stream), "adjoint: dots");
+  static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+  // forward: w0 -> w1 -> w2 -> w3 (S[0..3]), viscous factor, Brinkman -> S[4]
+  int rc = adj_to_spec(h, P[17], S[0], true);
+  for (int s = 0; s < 3 && !rc; ++s) rc = adj_forward_stage(h, kind, C, S[0], S[s], S[s + 1], A[s], B[s]);
+  if (!rc) rc = adj_combine(h, S[3], false, false, {{S[3], AM_VISC, 1.0}});
+  if (rc) return rc;
+  if (h->fac_b) {
+    rc = adj_to_phys(h, S[3], {D_U, D_V}, {P[0], P[1]});
+    if (!rc) rc = adj_scale(h, h->fac_b, P[0], 1.0, P[9], P[1], 1.0, P[10]);  // chi-factor times (u_total, v)
+    if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
+    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
+    if (!rc) rc = adj_combine(h, S[4], false, false, {{S[9], AM_IX, 1.0}, {S[8], AM_IY, -1.0}});
+  } else {
+    rc = adj_combine(h, S[4], false, false, {{S[3], AM_ONE, 1.0}});
+  }
+  if (rc) return rc;
+
+  // reverse: final projection (2/3 band, zero mean)
+  void* lam = S[5];
+  void* lam2 = S[6];
+  rc = adj_to_spec(h, P[18], lam, true);
+  if (!rc && h->fac_s) {
+    // w6 = T F[s w5]: d/drate = sum lam * (-chi_s dt s) * w5; lam <- T F[s lam]
+    rc = adj_to_phys(h, S[4], {D_W}, {P[0]});
+    if (!rc) rc = adj_to_phys(h, lam, {D_W}, {P[6]});
+    if (!rc) rc = adj_scale(h, h->fac_s, P[0], 1.0, P[1], P[6], 1.0, P[2]);
+    if (rc) return rc;
+    if (h->chi_s)
+      CK(h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                              dots + 3, h->stream)
+                 : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                               dots + 3, h->stream),
+         "adjoint: sponge-rate derivative");
+    rc = adj_to_spec(h, P[2], lam, false);
+  }
+  if (!rc && h->fac_b) {
+    // w5 = T (d_x (f v) - d_y (f u)): lam <- conj(dv) F[f (-lam_x)] - conj(du) F[f (-lam_y)]
+    rc = adj_to_phys(h, lam, {D_WX, D_WY}, {P[7], P[8]});
+    if (!rc) rc = adj_scale(h, h->fac_b, P[7], -1.0, P[9], P[8], -1.0, P[10]);
+    if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
+    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
+    if (!rc) rc = adj_combine(h, lam, false, false, {{S[8], AM_CV, 1.0}, {S[9], AM_CU, -1.0}});
+  }
+  if (!rc) rc = adj_combine(h, lam, false, false, {{lam, AM_VISC, 1.0}});
+  if (!rc) rc = adj_combine(h, S[7], false, false, {});
+  // the three stages in reverse: w_{s+1} = a_s w0 + b_s (w_s + dt L(w_s))
+  for (int s = 2; s >= 0 && !rc; --s) {
+    if (A[s] != 0.0) rc = adj_combine(h, S[7], true, false, {{lam, AM_ONE, A[s]}});
+    if (!rc) rc = adj_reverse_stage(h, kind, C, S[s], lam, lam2, B[s], s);
+    std::swap(lam, lam2);
+  }
+  if (!rc) rc = adj_combine(h, S[7], true, true, {{lam, AM_ONE, 1.0}});
+  if (!rc) rc = adj_to_phys(h, S[7], {D_W}, {P[18]});
+  return rc;
+}
+
 // physical field of the state into h->phys (working precision)
 int state_to_phys(qg_handle* h) {
   ColDesc c = col_base(h);
@@ -1025,6 +1319,10 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     for (size_t i = 0; i < f.size(); ++i)
       f[i] = ab2 ? params->dt * params->sponge_rate * sponge[i] : std::exp(-params->sponge_rate * sponge[i] * params->dt);
     if ((rc = upload_real(h, h->fac_s, f))) { delete h; return rc; }
+    if (!ab2) {
+      std::vector<double> cs(sponge, sponge + (size_t)n * n);
+      if ((rc = dalloc(h, &h->chi_s, phys_bytes)) || (rc = upload_real(h, h->chi_s, cs))) { delete h; return rc; }
+    }
   }
   // the zero state derives to zero fields: X already zeroed
   e = cudaStreamSynchronize(h->stream);
@@ -1325,5 +1623,65 @@ int qg_ensemble_sync(qg_ensemble* e, int32_t* first_bad) {
 }
 
 void qg_ensemble_destroy(qg_ensemble* e) { delete e; }
+
+int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* lam_n, int32_t on_device,
+                int32_t dtype, double* grads) {
+  if (!h || !omega_n || !lam_next || !lam_n) return fail(QG_ERR_ARG, "qg_step_vjp: NULL argument");
+  if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_step_vjp: bad dtype");
+  if (h->scheme != QG_SCHEME_RK3_EXACT)
+    return fail(QG_ERR_UNSUPPORTED, "qg_step_vjp: only the RK3 scheme has an adjoint");
+  if (h->cl.kind != QG_NONE && h->cl.kind != QG_SMAG && h->cl.kind != QG_LEITH)
+    return fail(QG_ERR_UNSUPPORTED, "qg_step_vjp: the dynamic closures have no adjoint");
+  int rc = adj_alloc(h);
+  if (rc) return rc;
+  auto& P = h->adj_P;
+  const size_t count = (size_t)h->g.n * h->g.n;
+  const int src32 = dtype == QG_FP32;
+  for (int k = 0; k < 2; ++k) {
+    const void* src = k ? lam_next : omega_n;
+    void* dst = P[17 + k];
+    if (on_device) {
+      CK(launch_convert(src, src32, dst, h->fp32, count, h->stream), "qg_step_vjp: convert");
+    } else if (src32 == h->fp32) {
+      CK(cudaMemcpyAsync(dst, src, count * h->esz, cudaMemcpyHostToDevice, h->stream), "qg_step_vjp: copy");
+      CK(cudaStreamSynchronize(h->stream), "qg_step_vjp: sync");
+    } else {
+      std::vector<double> v(count);
+      if (src32) for (size_t i = 0; i < count; ++i) v[i] = ((const float*)src)[i];
+      else std::memcpy(v.data(), src, count * 8);
+      if ((rc = upload_real(h, dst, v))) return rc;
+    }
+  }
+  if ((rc = adj_step(h))) return rc;
+  double d[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(d, h->adj_dots + kAdjDotBlocks, sizeof(d), cudaMemcpyDeviceToHost, h->stream),
+     "qg_step_vjp: derivatives");
+  const int dst32 = src32;
+  if (on_device) {
+    CK(launch_convert(P[18], h->fp32, lam_n, dst32, count, h->stream), "qg_step_vjp: convert out");
+    CK(cudaStreamSynchronize(h->stream), "qg_step_vjp: sync");
+  } else {
+    std::vector<unsigned char> tmp(count * h->esz);
+    CK(cudaMemcpyAsync(tmp.data(), P[18], tmp.size(), cudaMemcpyDeviceToHost, h->stream), "qg_step_vjp: copy out");
+    CK(cudaStreamSynchronize(h->stream), "qg_step_vjp: sync");
+    for (size_t i = 0; i < count; ++i) {
+      const double v = h->fp32 ? (double)((const float*)tmp.data())[i] : ((const double*)tmp.data())[i];
+      if (dst32) ((float*)lam_n)[i] = (float)v;
+      else ((double*)lam_n)[i] = v;
+    }
+  }
+  if (grads) {
+    const double dC = d[0] + d[1] + d[2];
+    grads[0] = dC;
+    grads[1] = 0.0;
+    if (h->cl.kind == QG_SMAG || h->cl.kind == QG_LEITH) {
+      const int p = h->cl.kind == QG_SMAG ? 2 : 3;
+      const double delta = h->L / h->g.n;
+      grads[1] = dC * p * std::pow(h->cl.c, p - 1) * std::pow(delta, p);
+    }
+    grads[2] = d[3];
+  }
+  return QG_OK;
+}
 
 }  // extern "C"

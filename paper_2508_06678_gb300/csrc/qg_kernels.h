@@ -24,6 +24,65 @@ template <typename T>
 cudaError_t launch_phys_maxabs(const Geom& g, const void* f, double* partials, int nblk, double* out,
                                cudaStream_t st);
 
+// ---- discrete adjoint of the step (adjoint.cu)
+// spectral multipliers of adj_combine (conjugates are the transposes the adjoint needs)
+enum AdjMul : int {
+  AM_ONE = 0,
+  AM_CU,    // -i k_y / |k|^2   transpose of w -> u
+  AM_CV,    // +i k_x / |k|^2   transpose of w -> v
+  AM_CX,    // -i k_x           transpose of d/dx
+  AM_CY,    // -i k_y           transpose of d/dy
+  AM_IX,    // +i k_x
+  AM_IY,    // +i k_y
+  AM_XY,    // k_x k_y / |k|^2           w -> psi_xy
+  AM_DD,    // (k_x^2 - k_y^2) / |k|^2   w -> psi_xx - psi_yy
+  AM_VISC,  // exp(-(nu |k|^2 + mu) dt)
+};
+constexpr int kAdjTerms = 12;
+struct AdjTerm {
+  const void* in;  // spectral array (stored band layout)
+  int code;        // AdjMul
+  double coef;
+};
+struct AdjCombine {
+  void* out;
+  int accumulate;  // out += sum (else out = sum)
+  int zero_mean;   // set the (0, 0) mode to zero
+  int nterm;
+  AdjTerm term[kAdjTerms];
+  double nu, mu, dt;  // AM_VISC
+};
+enum AdjKind : int { AK_NONE = 0, AK_SMAG = 1, AK_LEITH = 2 };
+enum AdjProdMode : int { AP_FORWARD = 0, AP_ADJOINT = 1 };
+// Pointwise products (physical arrays, working precision).
+//   forward: out0 = u w_x + v w_y, out1 = g w_x, out2 = g w_y
+//   adjoint: out0..3 = lam w_x, lam w_y, lam u, lam v; with a closure, p = -lam_x, q = -lam_y,
+//            s = p w_x + q w_y: Leith out4,5 = g p + s w_x / g, g q + s w_y / g;
+//            Smagorinsky out4,5 = g p, g q, out6,7 = 4 s psi_xy / g, s psi_d / g
+struct AdjProducts {
+  int kind, mode;
+  const void *u, *v, *wx, *wy, *pxy, *pd;
+  const void *lam, *lx, *ly;
+  void* out[8];
+};
+constexpr int kAdjDotBlocks = 256;
+
+template <typename T>
+cudaError_t launch_adj_combine(const Geom& g, const AdjCombine& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_products(size_t count, const AdjProducts& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_scale(size_t count, const void* f, const void* x0, double s0, void* out0, const void* x1,
+                             double s1, void* out1, cudaStream_t st);
+// out[0] = scale * sum_k w_k Re(A conj B) over the stored band (partials: kAdjDotBlocks doubles)
+template <typename T>
+cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, double scale, double* partials,
+                                double* out, cudaStream_t st);
+// out[0] = scale * sum_i X_i Y_i Z_i
+template <typename T>
+cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, double scale,
+                                double* partials, double* out, cudaStream_t st);
+
 // Sets the thread-local message returned by qg_last_error().
 void set_last_error(const char* msg);
 

@@ -16,7 +16,8 @@ from ._lib import (QG_ERR_NONFINITE, QG_FP32, QG_FP64, QG_OK, QGError, check, lo
                    qg_member, qg_params)
 
 __all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_step", "qg_sync", "qg_diagnostics", "qg_destroy",
-           "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_last_error", "qg_version", "QGSolver",
+           "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_step_vjp", "qg_last_error", "qg_version",
+           "QGSolver",
            "QGEnsemble"]
 
 
@@ -112,6 +113,31 @@ def qg_diagnostics(h: int, raise_nonfinite: bool = True) -> dict:
         check(rc, "qg_diagnostics")
     return {"t": d.t, "step": d.step, "energy": d.energy, "enstrophy": d.enstrophy, "coeff": d.coeff,
             "max_abs_omega": d.max_abs_omega, "finite": bool(d.finite)}
+
+
+def qg_step_vjp(h: int, n: int, omega_n, lam_next, lam_n=None):
+    """Vector-Jacobian product of one step; returns (lam_n, grads) with grads = {"C", "c", "sponge_rate"}.
+
+    omega_n and lam_next are both numpy arrays (host) or both torch CUDA
+    tensors of the same dtype; lam_n (optional) is the output buffer.
+    """
+    pa, dev_a, dt_a, ka = _buffer(omega_n, n)
+    pb, dev_b, dt_b, kb = _buffer(lam_next, n)
+    if dev_a != dev_b or dt_a != dt_b:
+        raise ValueError("omega_n and lam_next must share location and dtype")
+    if lam_n is None:
+        if dev_a:
+            import torch
+            lam_n = torch.empty_like(lam_next)
+        else:
+            lam_n = np.empty((n, n), dtype=np.float32 if dt_a == QG_FP32 else np.float64)
+    pc, dev_c, dt_c, kc = _buffer(lam_n, n)
+    if dev_c != dev_a or dt_c != dt_a:
+        raise ValueError("lam_n must share location and dtype with the inputs")
+    g = np.zeros(3)
+    check(load().qg_step_vjp(h, pa, pb, pc, dev_a, dt_a, g.ctypes.data_as(C.POINTER(C.c_double))), "qg_step_vjp")
+    del ka, kb, kc
+    return lam_n, {"C": float(g[0]), "c": float(g[1]), "sponge_rate": float(g[2])}
 
 
 def qg_destroy(h: int) -> None:
@@ -237,6 +263,9 @@ class QGSolver:
 
     def sync(self) -> None:
         qg_sync(self.h)
+
+    def step_vjp(self, omega_n, lam_next, lam_n=None):
+        return qg_step_vjp(self.h, self.cfg.n, omega_n, lam_next, lam_n)
 
     def diagnostics(self, raise_nonfinite: bool = True) -> dict:
         return qg_diagnostics(self.h, raise_nonfinite)
