@@ -589,12 +589,262 @@ def m_launches(m) -> int:
     """Kernel launches of one solver handle so far (every kernel class)."""
     import ctypes as C
     from paper_2508_06678_gb300._lib import load
-    counts = (C.c_int32 * 8)()
-    load().qg_kernel_times(m.h, counts, None, 8)
+    from paper_2508_06678_gb300._lib import KERNEL_CLASSES
+    nk = len(KERNEL_CLASSES)
+    counts = (C.c_int32 * nk)()
+    load().qg_kernel_times(m.h, counts, None, nk)
     return int(sum(counts))
 
 
+# ---------------------------------------------------------------------------
+# Adjoint: gradient of an MSE loss of a 256^2 Smagorinsky LES (FP64) against a
+# 1024^2 closure-free run filtered to 256^2 at steps 100, 120, ..., 400, with
+# respect to the initial field, c_S and the sponge rate; checkpoints every 20.
+# ---------------------------------------------------------------------------
+ADJ = {"n": 256, "n_fr": 1024, "steps": 400, "obs_first": 100, "obs_every": 20, "checkpoint": 20, "c": 0.17,
+       "seed": 5, "beta": 5.0, "U": 0.5, "radius": 0.4}
+ADJ_METRIC = ("grid-pt-steps/s of the loss gradient (forward + checkpointed adjoint), 256^2 Smagorinsky FP64 LES, "
+              "400 steps, MSE against a filtered 1024^2 run")
+
+
+def adjoint_workload():
+    c = ADJ
+    les = S.Workload("adjoint256-smag", c["n"], "island", beta=c["beta"], U=c["U"], closure=S.SMAG, c=c["c"],
+                     radius=c["radius"], seed=c["seed"])
+    fr = S.Workload("fr1024", c["n_fr"], "island", beta=c["beta"], U=c["U"], closure=S.NONE, radius=c["radius"],
+                    seed=c["seed"])
+    obs = list(range(c["obs_first"], c["steps"] + 1, c["obs_every"]))
+    return les, fr, obs
+
+
+def adjoint_targets(qg, fr, obs, stream):
+    """The 1024^2 run (FP32, no closure) at the observed steps, filtered to 256^2 (Eq. 5), and its filtered start."""
+    s = qg.QGSolver.from_workload(fr, precision=qg.QG_FP32, stream=stream)
+    w0 = fr.omega0()
+    s.set_state(w0)
+    snaps = []
+    k = 0
+    for t in obs:
+        s.step(t - k)
+        k = t
+        snaps.append(s.get_state())
+    s.close()
+    n = ADJ["n"]
+    return qg.qg_grid_filter(w0, n, fr.L), qg.qg_grid_filter(np.stack(snaps), n, fr.L)
+
+
+def time_adjoint_oracle(les, max_seconds: float):
+    import oracle as O
+    ops = O.Ops(les.n, les.L)
+    wh = O.project(ops, les.omega0())
+    lam = np.random.default_rng(0).standard_normal((les.n, les.n))
+    params = O.Params(dt=les.dt, nu=les.nu, mu=les.mu, eta=les.eta, sponge_rate=les.sponge_rate)
+    chi, chs = les.mask(), les.sponge_field()
+    cl = O.Closure(les.closure, c=les.c)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < max_seconds:
+        # per step of a checkpointed gradient: the forward run, its recomputation, one adjoint step
+        w1, _ = O.full_step(ops, wh, les.beta, les.U, cl, params, chi, chs)
+        O.full_step(ops, wh, les.beta, les.U, cl, params, chi, chs)
+        lam, _ = O.full_step_vjp(ops, wh, lam, les.beta, les.U, cl, params, chi, chs)
+        wh = w1
+        done += 1
+    return done, time.perf_counter() - t0
+
+
+def run_adjoint_reference(args, budget):
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    les, _, _ = adjoint_workload()
+    done, el = time_adjoint_oracle(les, budget)
+    value = les.n * les.n * done / el
+    line = {
+        "metric": ADJ_METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": done,
+        "warmup": 0, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": "adjoint256", **ADJ},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward steps "
+                                   f"+ 1 full_step_vjp each) of the 256^2 LES, {el:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint_bench(args):
+    import torch
+    import torch.distributed as dist
+    import ctypes as C
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2508_06678_gb300 as qg
+    from paper_2508_06678_gb300._lib import KERNEL_CLASSES, LIB_PATH, load
+    from paper_2508_06678_gb300.adjoint import rollout_grad
+    if not os.path.exists(LIB_PATH):
+        from paper_2508_06678_gb300.build import build
+        build()
+    lib = load()
+    les, fr, obs = adjoint_workload()
+    stream = torch.cuda.Stream()
+    w0_les, targets = adjoint_targets(qg, fr, obs, stream)
+    n, K, ce = les.n, ADJ["steps"], ADJ["checkpoint"]
+    solver = qg.QGSolver.from_workload(les, precision=qg.QG_FP64, stream=stream)
+    tgt = {k: torch.from_numpy(t).cuda() for k, t in zip(obs, targets)}
+    w0 = torch.from_numpy(w0_les).cuda()
+    scale = 2.0 / (len(obs) * n * n)
+
+    need = sorted(set(range(0, K, ce)) | set(obs))
+
+    def forward(w_start):
+        """One forward run keeping the checkpoints and the observed states."""
+        solver.set_state(w_start)
+        ckpts, states = {}, {}
+        k = 0
+        for t in need:
+            solver.step(t - k)
+            k = t
+            st_ = solver.get_state(out=torch.empty((n, n), dtype=torch.float64, device="cuda"))
+            if t % ce == 0 and t < K:
+                ckpts[t] = st_
+            if t in tgt:
+                states[t] = st_
+        return ckpts, states
+
+    def gradient():
+        ckpts, states = forward(w0)
+        # dloss/dw_k of loss = mean over the observed steps and points of (w_k - target_k)^2
+        g_obs = {t: scale * (states[t] - tgt[t]) for t in obs}
+        loss = float(sum(((states[t] - tgt[t]) ** 2).sum().item() for t in obs)) * scale / 2.0
+        lam, g = rollout_grad(solver, None, K, g_obs, ce, ckpts=ckpts)
+        return loss, lam, g
+
+    for _ in range(max(1, args.warmup // 3)):
+        loss, lam, g = gradient()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except (AttributeError, RuntimeError):
+        gpu_id = str(local)
+    reps = max(1, args.steps)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        loss, lam, g = gradient()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / reps)
+    value = world * n * n * K / (ms / 1e3)
+
+    # the plain forward run and one adjoint step, for the cost ratio
+    solver.set_state(w0)
+    solver.step(5)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / K
+    st = solver.get_state(out=torch.empty((n, n), dtype=torch.float64, device="cuda"))
+    lam1 = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        solver.step_vjp(st, lam1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(50):
+        solver.step_vjp(st, lam1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vjp_ms = e0.elapsed_time(e1) / 50
+
+    # per-class device times of adjoint steps (eager, a CUDA event pair around every launch)
+    nk = len(KERNEL_CLASSES)
+    lib.qg_profile(solver.h, 1)
+    for _ in range(5):
+        solver.step_vjp(st, lam1)
+    counts = (C.c_int32 * nk)()
+    kms = (C.c_double * nk)()
+    lib.qg_kernel_times(solver.h, counts, kms, nk)
+    lib.qg_profile(solver.h, 0)
+    cls = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(nk) if counts[i]}
+    Kb = (n - 1) // 3
+    I = n * (Kb + 1) * 16
+    R = n * n * 8
+    n_row, t_row = cls.get("adj_row", (0, 0.0))
+    achieved = (R + I) * n_row / (t_row / 1e3) / 1e9 if t_row else 0.0
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "adj_row (row pass of one field into or out of physical space)",
+                "peak_source": peak_src, "bytes_per_launch": R + I,
+                "avg_launch_us": 1e3 * t_row / n_row if n_row else None,
+                "class_ms_per_vjp": {k: v[1] / 5 for k, v in cls.items()},
+                "class_launches_per_vjp": {k: v[0] / 5 for k, v in cls.items()},
+                "note": "256^2 FP64 fields (0.5 MB) stay in the 126 MB L2: these launches are latency-bound",
+                "measured_in": "CUDA events around each launch of 5 eager adjoint steps"}
+
+    # end to end: host initial field and targets in, gradient out
+    barrier()
+    t0 = time.perf_counter()
+    w_host = w0_les.copy()
+    tg_host = {k: t.copy() for k, t in zip(obs, targets)}
+    tgt = {k: torch.from_numpy(t).cuda() for k, t in tg_host.items()}
+    ck, states = forward(torch.from_numpy(w_host).cuda())
+    g_obs = {t: scale * (states[t] - tgt[t]) for t in obs}
+    lam_h, _ = rollout_grad(solver, None, K, g_obs, ce, ckpts=ck)
+    lam_h = lam_h.cpu().numpy()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            done, el = time_adjoint_oracle(les, args.cpu_seconds)
+            cpu = {"value": n * n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward steps + 1 "
+                             f"full_step_vjp each) of the 256^2 LES, {el:.1f} s"}
+        line = {
+            "metric": ADJ_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "adjoint256", **ADJ, "observed_steps": len(obs), "loss": loss,
+                       "grad_norm": float(lam.norm().item()), "dloss_dc": g["c"], "dloss_drate": g["sponge_rate"],
+                       "ms_per_gradient": ms, "forward_ms_per_step": fwd_ms, "vjp_ms_per_step": vjp_ms,
+                       "adjoint_over_forward": vjp_ms / fwd_ms,
+                       "gradient_over_forward_run": ms / (fwd_ms * K),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "256^2 working set fits the L2 (latency-bound sizes)"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * n * n * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": (len(obs) + 1) * R / K,
+                    "d2h_bytes_per_step": (len(obs) + 1) * R / K,
+                    "api": "initial field and targets from host, rollout + qg_step_vjp sweep, gradient to host"},
+            "gpu_launches": int(sum(v[0] for v in cls.values()) / 5 * K), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 TOOLS = {"series512": {"ours": run_series_bench, "reference": run_series_reference},
+         "adjoint256": {"ours": run_adjoint_bench, "reference": run_adjoint_reference},
          "ensemble96": {"ours": run_ensemble_bench, "reference": run_ensemble_reference}}
 
 
@@ -694,9 +944,10 @@ def main():
     lib.qg_profile(qg_h, 1)
     torch.cuda.synchronize()
     solver.step(args.steps)
-    counts = (C.c_int32 * 8)()
-    kms = (C.c_double * 8)()
-    lib.qg_kernel_times(qg_h, counts, kms, 8)
+    nk = len(KERNEL_CLASSES)
+    counts = (C.c_int32 * nk)()
+    kms = (C.c_double * nk)()
+    lib.qg_kernel_times(qg_h, counts, kms, nk)
     lib.qg_profile(qg_h, 0)
     solver.sync()
     launches = int(sum(counts))  # our kernels per K-step pass (the timed pass launches the same)
@@ -704,7 +955,7 @@ def main():
     # ---- roofline of the dominant kernel class
     peaks, peak_src = measured_peaks()
     model = algorithmic_bytes(wl, fp32) if scheme == 0 else algorithmic_bytes_ab2cn(wl, fp32)
-    per_class = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(8)}
+    per_class = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(nk)}
     dom = max((k for k in per_class if per_class[k][0] > 0 and k in model), key=lambda k: per_class[k][1])
     n_l, t_l = per_class[dom]
     avg_s = t_l / n_l / 1e3

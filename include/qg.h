@@ -274,7 +274,8 @@ void qg_ensemble_destroy(qg_ensemble* e);
  *             for C = (c Delta)^p, d loss / d sponge_rate.
  * The forward stages are recomputed from omega_n; the handle's own state and
  * stepping are untouched.  Synchronous on the handle's stream; the first call
- * allocates a workspace of 19 spectral, 19 physical and 6 mixed arrays.
+ * allocates a workspace of 25 spectral, 37 physical and 6 mixed arrays; later
+ * calls replay one captured CUDA graph.
  * QG_ERR_UNSUPPORTED for the dynamic closures and for the AB2CN scheme. */
 int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* lam_n, int32_t on_device,
                 int32_t dtype, double* grads);
@@ -288,7 +289,10 @@ int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* l
 #define QG_K_ROW_SPONGE 5  /* row pass of the sponge sub-step (Eq. 3) */
 #define QG_K_COL_FINAL 6   /* column pass: projection of w^{n+1}, stage-1 fields */
 #define QG_K_OTHER 7       /* state I/O and diagnostics */
-#define QG_NUM_KCLASS 8
+#define QG_K_ADJ_ROW 8     /* qg_step_vjp: row passes (one field each, into or out of physical space) */
+#define QG_K_ADJ_COL 9     /* qg_step_vjp: column passes (forward transforms, derived fields) */
+#define QG_K_ADJ_PW 10     /* qg_step_vjp: pointwise products, spectral multipliers, inner products */
+#define QG_NUM_KCLASS 11
 
 /* Tracing.  enable = 1 clears the counters and starts recording a CUDA event
  * pair around every kernel launch on the handle's stream; 0 stops recording.

@@ -24,7 +24,7 @@ QG_SCHEME_RK3_EXACT = 0
 QG_SCHEME_AB2CN = 1
 QG_NONE, QG_SMAG, QG_LEITH, QG_DSMAG, QG_DLEITH = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("row_stage", "col_reduce", "col_stage", "row_brinkman", "col_curl", "row_sponge", "col_final",
-                  "other")
+                  "other", "adj_row", "adj_col", "adj_pointwise")
 
 ERROR_NAMES = {
     QG_ERR_ARG: "QG_ERR_ARG", QG_ERR_CUDA: "QG_ERR_CUDA", QG_ERR_NONFINITE: "QG_ERR_NONFINITE",

@@ -272,17 +272,23 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
       cx.bad |= !isfinite(x[m].x) | !isfinite(x[m].y);
     }
     cx.fwd_store(x, d.out[0], d.nout > 1 ? d.out[1] : nullptr, false, false);
-  } else {  // RP_COPY: physical row in or out
+  } else {  // RP_COPY: one or two physical rows in or out (two as the real and imaginary parts of one FFT)
     if (d.in_phys) {
       const T* src = reinterpret_cast<const T*>(d.phys_in) + yN;
+      const T* src2 = d.phys_in2 ? reinterpret_cast<const T*>(d.phys_in2) + yN : nullptr;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = mk<C>(src[t + TT * m], T(0));
-      cx.fwd_store(x, d.out[0], nullptr, false, false);
+      for (int m = 0; m < 16; ++m) x[m] = mk<C>(src[t + TT * m], src2 ? src2[t + TT * m] : T(0));
+      cx.fwd_store(x, d.out[0], src2 ? d.out[1] : nullptr, false, false);
     } else {
-      cx.inv_pair(x, d.in[0], nullptr);
+      cx.inv_pair(x, d.in[0], d.phys_out2 ? d.in[1] : nullptr);
       T* dst = reinterpret_cast<T*>(d.phys_out) + yN;
 #pragma unroll
       for (int m = 0; m < 16; ++m) dst[t + TT * m] = x[m].x;
+      if (d.phys_out2) {
+        T* dst2 = reinterpret_cast<T*>(d.phys_out2) + yN;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) dst2[t + TT * m] = x[m].y;
+      }
     }
   }
   if (d.check_finite && d.flag) {

@@ -205,6 +205,9 @@ struct qg_handle {
   // workspace of qg_step_vjp, allocated by its first call: spectral, physical and mixed arrays, dot results
   std::vector<void*> adj_S, adj_P, adj_M;
   double* adj_dots = nullptr;
+  cudaGraphExec_t adj_graph = nullptr;  // one adjoint step, captured after its first eager run
+  bool adj_graph_tried = false;
+  int32_t adj_graph_launches[QG_NUM_KCLASS] = {};
   void* tw = nullptr;
   void* ptw = nullptr;  // per-pass twiddle table of the power-of-two kernels
   void* visc_x = nullptr;
@@ -239,6 +242,7 @@ struct qg_handle {
 
   ~qg_handle() {
     if (step_graph) cudaGraphExecDestroy(step_graph);
+    if (adj_graph) cudaGraphExecDestroy(adj_graph);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -691,9 +695,11 @@ int enqueue_any_step(qg_handle* h) { return h->scheme == QG_SCHEME_AB2CN ? enque
 // state: conjugate multipliers for the spectral operators, pointwise products
 // for the nonlinear terms (Eq. 1, 9, 10, 13).
 // ---------------------------------------------------------------------------
-constexpr int kAdjNS = 19;  // spectral: w0..w3, w5, lam, lam', acc, 11 product / SGS spectra
-constexpr int kAdjNP = 19;  // physical: 6 forward fields, 3 adjoint fields, 8 products, input, output
+constexpr int kAdjNS = 25;  // spectral: w0..w3, w5, lam, lam', acc, 11 product spectra, 3 x 2 stage SGS fluxes
+constexpr int kAdjNP = 37;  // physical: 6 fields, 3 adjoint fields, 8 products, input, output, 3 x 6 stage fields
 constexpr int kAdjNM = 6;   // mixed: the outputs of one derive pass
+constexpr int kAdjStageP = 19;  // first of the per-stage physical fields (u, v, w_x, w_y, psi_xy, psi_d)
+constexpr int kAdjStageS = 19;  // first of the per-stage spectral SGS fluxes F[g w_x], F[g w_y]
 
 int adj_alloc(qg_handle* h) {
   if (!h->adj_S.empty()) return QG_OK;
@@ -729,7 +735,7 @@ int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   r.in_phys = 1;
   r.phys_in = P;
   r.out[0] = h->adj_M[0];
-  int rc = run_row(h, r, QG_K_OTHER, false);
+  int rc = run_row(h, r, QG_K_ADJ_ROW, false);
   if (rc) return rc;
   ColDesc c = col_base(h);
   c.op = CO_FORWARD;
@@ -739,10 +745,42 @@ int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   c.store_w0 = 1;
   c.zero_mean = zero_mean ? 1 : 0;
   c.nder = 0;
-  return run_col(h, c, QG_K_OTHER, false);
+  return run_col(h, c, QG_K_ADJ_COL, false);
 }
 
-// physical fields of derived spectra (codes D_W, D_U (with U), D_V, D_WX, D_WY, D_PXY, D_PD) of a spectral state
+// spectral bands of several physical fields: row passes take them in pairs (one complex FFT per pair)
+int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::initializer_list<void*> S) {
+  std::vector<const void*> p(P);
+  std::vector<void*> s(S);
+  int rc = QG_OK;
+  for (size_t i = 0; i < p.size() && !rc; i += 2) {
+    const bool two = i + 1 < p.size();
+    RowDesc r{};
+    r.prog = RP_COPY;
+    r.nin = 1;
+    r.nout = two ? 2 : 1;
+    r.in_phys = 1;
+    r.phys_in = p[i];
+    r.phys_in2 = two ? p[i + 1] : nullptr;
+    r.out[0] = h->adj_M[0];
+    r.out[1] = h->adj_M[1];
+    rc = run_row(h, r, QG_K_ADJ_ROW, false);
+    for (int k = 0; k < (two ? 2 : 1) && !rc; ++k) {
+      ColDesc c = col_base(h);
+      c.op = CO_FORWARD;
+      c.nfwd = 1;
+      c.fin[0] = h->adj_M[k];
+      c.w0 = s[i + k];
+      c.store_w0 = 1;
+      c.nder = 0;
+      rc = run_col(h, c, QG_K_ADJ_COL, false);
+    }
+  }
+  return rc;
+}
+
+// physical fields of derived spectra (codes D_W, D_U (with U), D_V, D_WX, D_WY, D_PXY, D_PD) of a spectral
+// state: one derive pass, then row passes in pairs
 int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, std::initializer_list<void*> P) {
   ColDesc c = col_base(h);
   c.op = CO_DERIVE;
@@ -753,18 +791,20 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
     c.dout[c.nder] = h->adj_M[c.nder];
     ++c.nder;
   }
-  int rc = run_col(h, c, QG_K_OTHER, false);
-  int i = 0;
-  for (void* dst : P) {
-    if (rc) return rc;
+  int rc = run_col(h, c, QG_K_ADJ_COL, false);
+  std::vector<void*> dst(P);
+  for (size_t i = 0; i < dst.size() && !rc; i += 2) {
+    const bool two = i + 1 < dst.size();
     RowDesc r{};
     r.prog = RP_COPY;
-    r.nin = 1;
+    r.nin = two ? 2 : 1;
     r.nout = 1;
-    r.in[0] = h->adj_M[i++];
+    r.in[0] = h->adj_M[i];
+    r.in[1] = two ? h->adj_M[i + 1] : nullptr;
     r.out_phys = 1;
-    r.phys_out = dst;
-    rc = run_row(h, r, QG_K_OTHER, false);
+    r.phys_out = dst[i];
+    r.phys_out2 = two ? dst[i + 1] : nullptr;
+    rc = run_row(h, r, QG_K_ADJ_ROW, false);
   }
   return rc;
 }
@@ -779,46 +819,56 @@ int adj_combine(qg_handle* h, void* out, bool accumulate, bool zero_mean,
   a.nu = h->par.nu;
   a.mu = h->par.mu;
   a.dt = h->par.dt;
-  CK(h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream),
-     "adjoint: combine");
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e =
+      h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream);
+  br.done();
+  CK(e, "adjoint: combine");
   return QG_OK;
 }
 
 int adj_products(qg_handle* h, AdjProducts a) {
   const size_t count = (size_t)h->g.n * h->g.n;
-  CK(h->fp32 ? launch_adj_products<float>(count, a, h->stream) : launch_adj_products<double>(count, a, h->stream),
-     "adjoint: products");
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e =
+      h->fp32 ? launch_adj_products<float>(count, a, h->stream) : launch_adj_products<double>(count, a, h->stream);
+  br.done();
+  CK(e, "adjoint: products");
   return QG_OK;
 }
 
 int adj_scale(qg_handle* h, const void* f, const void* x0, double s0, void* out0, const void* x1, double s1,
               void* out1) {
   const size_t count = (size_t)h->g.n * h->g.n;
-  CK(h->fp32 ? launch_adj_scale<float>(count, f, x0, s0, out0, x1, s1, out1, h->stream)
-             : launch_adj_scale<double>(count, f, x0, s0, out0, x1, s1, out1, h->stream),
-     "adjoint: scale");
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e = h->fp32 ? launch_adj_scale<float>(count, f, x0, s0, out0, x1, s1, out1, h->stream)
+                                : launch_adj_scale<double>(count, f, x0, s0, out0, x1, s1, out1, h->stream);
+  br.done();
+  CK(e, "adjoint: scale");
   return QG_OK;
 }
 
-// the forward products of a stage state's spectral fields: J, and g w_x, g w_y with a closure
-int adj_stage_fields(qg_handle* h, const void* Sw, int kind) {
+// the physical fields u_total, v, w_x, w_y (and psi_xy, psi_d for Smagorinsky) of a stage state, kept per stage
+// for the reverse sweep (first of six arrays at P[f0])
+int adj_stage_fields(qg_handle* h, const void* Sw, int kind, int f0) {
   auto& P = h->adj_P;
   if (kind == AK_SMAG)
-    return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY, D_PXY, D_PD}, {P[0], P[1], P[2], P[3], P[4], P[5]});
-  return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY}, {P[0], P[1], P[2], P[3]});
+    return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY, D_PXY, D_PD},
+                       {P[f0], P[f0 + 1], P[f0 + 2], P[f0 + 3], P[f0 + 4], P[f0 + 5]});
+  return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY}, {P[f0], P[f0 + 1], P[f0 + 2], P[f0 + 3]});
 }
 
-AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode) {
+AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0) {
   auto& P = h->adj_P;
   AdjProducts a{};
   a.kind = kind;
   a.mode = mode;
-  a.u = P[0];
-  a.v = P[1];
-  a.wx = P[2];
-  a.wy = P[3];
-  a.pxy = P[4];
-  a.pd = P[5];
+  a.u = P[f0];
+  a.v = P[f0 + 1];
+  a.wx = P[f0 + 2];
+  a.wy = P[f0 + 3];
+  a.pxy = P[f0 + 4];
+  a.pd = P[f0 + 5];
   a.lam = P[6];
   a.lx = P[7];
   a.ly = P[8];
@@ -826,41 +876,41 @@ AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode) {
   return a;
 }
 
-// L(w) = -J - beta psi_x + C div(g grad w) of the stage state Sw into spectral Sout scaled as
-// Sout = a w0 + b (ws + dt L(ws)) (Shu-Osher stage); spectra S[8..10] are scratch
+// L(w) = -J - beta psi_x + C div(g grad w) of stage s's state Sw into spectral Sout scaled as
+// Sout = a w0 + b (ws + dt L(ws)) (Shu-Osher stage); keeps the stage's fields and SGS flux spectra
 int adj_forward_stage(qg_handle* h, int kind, double C, const void* S0, const void* Sw, void* Sout, double a,
-                      double b) {
+                      double b, int s) {
   auto& S = h->adj_S;
   auto& P = h->adj_P;
   const double dt = h->par.dt;
-  int rc = adj_stage_fields(h, Sw, kind);
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD));
-  if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
-  if (kind != AK_NONE) {
-    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
-    if (!rc) rc = adj_to_spec(h, P[11], S[10], false);
-  }
+  const int f0 = kAdjStageP + 6 * s;
+  void* Sgx = S[kAdjStageS + 2 * s];
+  void* Sgy = S[kAdjStageS + 2 * s + 1];
+  int rc = adj_stage_fields(h, Sw, kind, f0);
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
+  if (!rc) rc = kind == AK_NONE ? adj_to_spec_many(h, {P[9]}, {S[8]})
+                                 : adj_to_spec_many(h, {P[9], P[10], P[11]}, {S[8], Sgx, Sgy});
   if (rc) return rc;
   if (kind == AK_NONE)
     return adj_combine(h, Sout, false, false,
                        {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta}});
   return adj_combine(h, Sout, false, false,
                      {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta},
-                      {S[9], AM_IX, b * dt * C}, {S[10], AM_IY, b * dt * C}});
+                      {Sgx, AM_IX, b * dt * C}, {Sgy, AM_IY, b * dt * C}});
 }
 
 // Slam_out = b lam + L'(ws)^T (b dt lam) (one Shu-Osher stage in reverse); the derivative in C,
 // b dt sum(lam * div(g grad ws)), goes to adj_dots[slot]
-int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Sw, const void* Slam, void* Slam_out, double b,
-                      int slot) {
+int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Slam, void* Slam_out, double b, int slot) {
   auto& S = h->adj_S;
   auto& P = h->adj_P;
   const double dt = h->par.dt, bd = b * dt;
-  int rc = adj_stage_fields(h, Sw, kind);
-  if (!rc) rc = adj_to_phys(h, Slam, {D_W, D_WX, D_WY}, {P[6], P[7], P[8]});
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT));
-  const int nprod = kind == AK_NONE ? 4 : (kind == AK_LEITH ? 6 : 8);
-  for (int k = 0; k < nprod && !rc; ++k) rc = adj_to_spec(h, P[9 + k], S[8 + k], false);
+  const int f0 = kAdjStageP + 6 * slot;  // the stage's fields, kept by the forward recomputation
+  int rc = adj_to_phys(h, Slam, {D_W, D_WX, D_WY}, {P[6], P[7], P[8]});
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, f0));
+  if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12]}, {S[8], S[9], S[10], S[11]});
+  if (!rc && kind != AK_NONE) rc = adj_to_spec_many(h, {P[13], P[14]}, {S[12], S[13]});
+  if (!rc && kind == AK_SMAG) rc = adj_to_spec_many(h, {P[15], P[16]}, {S[14], S[15]});
   if (rc) return rc;
   AdjCombine a{};
   a.out = Slam_out;
@@ -884,21 +934,27 @@ int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Sw, const vo
       add(S[15], AM_DD, bd * C);
     }
   }
-  CK(h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream),
-     "adjoint: stage combine");
+  {
+    Bracket br(h, QG_K_ADJ_PW);
+    const cudaError_t e =
+        h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream);
+    br.done();
+    CK(e, "adjoint: stage combine");
+  }
   if (kind != AK_NONE) {
     // derivative in C: sum over points of lam * T div(g grad ws) (Parseval over the band)
-    rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD));
-    if (!rc) rc = adj_to_spec(h, P[10], S[16], false);
-    if (!rc) rc = adj_to_spec(h, P[11], S[17], false);
-    if (!rc) rc = adj_combine(h, S[18], false, false, {{S[16], AM_IX, 1.0}, {S[17], AM_IY, 1.0}});
+    rc = adj_combine(h, S[18], false, false,
+                     {{S[kAdjStageS + 2 * slot], AM_IX, 1.0}, {S[kAdjStageS + 2 * slot + 1], AM_IY, 1.0}});
     if (rc) return rc;
     const double n2 = double(h->g.n) * double(h->g.n);
-    CK(h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots, h->adj_dots + kAdjDotBlocks + slot,
-                                            h->stream)
-               : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
-                                             h->adj_dots + kAdjDotBlocks + slot, h->stream),
-       "adjoint: C derivative");
+    Bracket br(h, QG_K_ADJ_PW);
+    const cudaError_t e =
+        h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots,
+                                             h->adj_dots + kAdjDotBlocks + slot, h->stream)
+                : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
+                                              h->adj_dots + kAdjDotBlocks + slot, h->stream);
+    br.done();
+    CK(e, "adjoint: C derivative");
   }
   return QG_OK;
 }
@@ -916,14 +972,13 @@ int adj_step(qg_handle* h) {
   static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
   // forward: w0 -> w1 -> w2 -> w3 (S[0..3]), viscous factor, Brinkman -> S[4]
   int rc = adj_to_spec(h, P[17], S[0], true);
-  for (int s = 0; s < 3 && !rc; ++s) rc = adj_forward_stage(h, kind, C, S[0], S[s], S[s + 1], A[s], B[s]);
+  for (int s = 0; s < 3 && !rc; ++s) rc = adj_forward_stage(h, kind, C, S[0], S[s], S[s + 1], A[s], B[s], s);
   if (!rc) rc = adj_combine(h, S[3], false, false, {{S[3], AM_VISC, 1.0}});
   if (rc) return rc;
   if (h->fac_b) {
     rc = adj_to_phys(h, S[3], {D_U, D_V}, {P[0], P[1]});
     if (!rc) rc = adj_scale(h, h->fac_b, P[0], 1.0, P[9], P[1], 1.0, P[10]);  // chi-factor times (u_total, v)
-    if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
-    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
+    if (!rc) rc = adj_to_spec_many(h, {P[9], P[10]}, {S[8], S[9]});
     if (!rc) rc = adj_combine(h, S[4], false, false, {{S[9], AM_IX, 1.0}, {S[8], AM_IY, -1.0}});
   } else {
     rc = adj_combine(h, S[4], false, false, {{S[3], AM_ONE, 1.0}});
@@ -940,20 +995,23 @@ int adj_step(qg_handle* h) {
     if (!rc) rc = adj_to_phys(h, lam, {D_W}, {P[6]});
     if (!rc) rc = adj_scale(h, h->fac_s, P[0], 1.0, P[1], P[6], 1.0, P[2]);
     if (rc) return rc;
-    if (h->chi_s)
-      CK(h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                              dots + 3, h->stream)
-                 : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                               dots + 3, h->stream),
-         "adjoint: sponge-rate derivative");
+    if (h->chi_s) {
+      Bracket br(h, QG_K_ADJ_PW);
+      const cudaError_t e =
+          h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                               dots + 3, h->stream)
+                  : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                                dots + 3, h->stream);
+      br.done();
+      CK(e, "adjoint: sponge-rate derivative");
+    }
     rc = adj_to_spec(h, P[2], lam, false);
   }
   if (!rc && h->fac_b) {
     // w5 = T (d_x (f v) - d_y (f u)): lam <- conj(dv) F[f (-lam_x)] - conj(du) F[f (-lam_y)]
     rc = adj_to_phys(h, lam, {D_WX, D_WY}, {P[7], P[8]});
     if (!rc) rc = adj_scale(h, h->fac_b, P[7], -1.0, P[9], P[8], -1.0, P[10]);
-    if (!rc) rc = adj_to_spec(h, P[9], S[8], false);
-    if (!rc) rc = adj_to_spec(h, P[10], S[9], false);
+    if (!rc) rc = adj_to_spec_many(h, {P[9], P[10]}, {S[8], S[9]});
     if (!rc) rc = adj_combine(h, lam, false, false, {{S[8], AM_CV, 1.0}, {S[9], AM_CU, -1.0}});
   }
   if (!rc) rc = adj_combine(h, lam, false, false, {{lam, AM_VISC, 1.0}});
@@ -961,12 +1019,38 @@ int adj_step(qg_handle* h) {
   // the three stages in reverse: w_{s+1} = a_s w0 + b_s (w_s + dt L(w_s))
   for (int s = 2; s >= 0 && !rc; --s) {
     if (A[s] != 0.0) rc = adj_combine(h, S[7], true, false, {{lam, AM_ONE, A[s]}});
-    if (!rc) rc = adj_reverse_stage(h, kind, C, S[s], lam, lam2, B[s], s);
+    if (!rc) rc = adj_reverse_stage(h, kind, C, lam, lam2, B[s], s);
     std::swap(lam, lam2);
   }
   if (!rc) rc = adj_combine(h, S[7], true, true, {{lam, AM_ONE, 1.0}});
   if (!rc) rc = adj_to_phys(h, S[7], {D_W}, {P[18]});
   return rc;
+}
+
+// Capture one adjoint step (fixed workspace, so every call replays the same graph).
+void adj_build_graph(qg_handle* h) {
+  h->adj_graph_tried = true;
+  if (!h->stream || getenv("QG_NO_GRAPH")) return;
+  int32_t saved[QG_NUM_KCLASS];
+  memcpy(saved, h->launches, sizeof(saved));
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int rc = adj_step(h);
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  for (int i = 0; i < QG_NUM_KCLASS; ++i) h->adj_graph_launches[i] = h->launches[i] - saved[i];
+  memcpy(h->launches, saved, sizeof(saved));
+  if (rc != QG_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) h->adj_graph = ex;
+  cudaGraphDestroy(g);
+  cudaGetLastError();
 }
 
 // physical field of the state into h->phys (working precision)
@@ -1652,7 +1736,13 @@ int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* l
       if ((rc = upload_real(h, dst, v))) return rc;
     }
   }
-  if ((rc = adj_step(h))) return rc;
+  if (!h->prof && h->adj_graph) {
+    CK(cudaGraphLaunch(h->adj_graph, h->stream), "qg_step_vjp: graph launch");
+    for (int c = 0; c < QG_NUM_KCLASS; ++c) h->launches[c] += h->adj_graph_launches[c];
+  } else {
+    if ((rc = adj_step(h))) return rc;
+    if (!h->prof && !h->adj_graph_tried) adj_build_graph(h);
+  }
   double d[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(d, h->adj_dots + kAdjDotBlocks, sizeof(d), cudaMemcpyDeviceToHost, h->stream),
      "qg_step_vjp: derivatives");

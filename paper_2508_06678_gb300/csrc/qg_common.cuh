@@ -117,6 +117,8 @@ struct RowDesc {
   void* out[kMaxOut];
   const void* phys_in;
   void* phys_out;
+  const void* phys_in2;  // RP_COPY: a second physical field, transformed with the first (Hermitian pair)
+  void* phys_out2;       // RP_COPY: the second field of an inverse pair
   const void* factor;  // RP_SCALE: physical factor field
   int check_finite;    // set *flag if a product is not finite
   int* flag;

@@ -54,6 +54,10 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
   if (d.in_phys) {
     const T* src = reinterpret_cast<const T*>(d.phys_in) + (size_t)y * N;
     for (int x = tid; x < N; x += nt) slots[x] = src[x];
+    if (d.phys_in2) {
+      const T* src2 = reinterpret_cast<const T*>(d.phys_in2) + (size_t)y * N;
+      for (int x = tid; x < N; x += nt) slots[N + x] = src2[x];
+    }
   } else {
     for (int p = 0; p < d.nin; p += 2) {
       const C* A = reinterpret_cast<const C*>(d.in[p]) + (size_t)y * g.IP;
@@ -148,6 +152,10 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
     __syncthreads();
     T* dst = reinterpret_cast<T*>(d.phys_out) + (size_t)y * N;
     for (int x = tid; x < N; x += nt) dst[x] = slots[x];
+    if (d.phys_out2) {
+      T* dst2 = reinterpret_cast<T*>(d.phys_out2) + (size_t)y * N;
+      for (int x = tid; x < N; x += nt) dst2[x] = slots[N + x];
+    }
     return;
   }
   const T ks = T(g.kscale);
