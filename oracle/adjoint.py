@@ -19,8 +19,9 @@ in the reverse order of the forward operations; nonlinear terms are
 linearised at the forward fields, recomputed from w_n.
 
 Closures covered: none, Smagorinsky and Leith with a fixed coefficient
-C = (c Delta)^p (Eq. 10, 13).  The dynamic closures' coefficient (Eq. 12, 14)
-is not differentiated here.
+C = (c Delta)^p (Eq. 10, 13), and their dynamic forms, whose coefficient
+C(w) = max(0, <HM>/<MM>) (Eq. 12, 14) is differentiated through the quotient
+(zero gradient where it is clipped).
 
 Parity: pinned by central finite differences of the forward oracle (which is
 pinned by its own tests) in every direction the gradients cover.
@@ -29,13 +30,13 @@ from __future__ import annotations
 
 import numpy as np
 
-from .qg import (LEITH, NONE, RK3_STAGES, SMAG, Closure, Ops, Params, brinkman_substep, closure_power, explicit_rhs,
-                 gradient_magnitude, project, sgs_divergence_hat, sponge_substep, strain_magnitude, velocity,
-                 viscous_substep, vorticity_gradient)
+from .qg import (DLEITH, DSMAG, LEITH, NONE, RK3_STAGES, SMAG, Closure, Ops, Params, brinkman_substep,
+                 closure_power, explicit_rhs, germano_coefficient, gradient_magnitude, jacobian_hat, project,
+                 sgs_divergence_hat, sponge_substep, strain_magnitude, velocity, viscous_substep, vorticity_gradient)
 
-__all__ = ["rhs_vjp", "full_step_vjp", "ADJOINT_CLOSURES"]
+__all__ = ["jac_vjp", "sgs_vjp", "germano_vjp", "rhs_vjp", "full_step_vjp", "ADJOINT_CLOSURES"]
 
-ADJOINT_CLOSURES = (NONE, SMAG, LEITH)
+ADJOINT_CLOSURES = (NONE, SMAG, LEITH, DSMAG, DLEITH)
 
 
 def _multipliers(ops: Ops):
@@ -55,48 +56,96 @@ def _safe_ratio(a: np.ndarray, g: np.ndarray) -> np.ndarray:
     return out
 
 
-def rhs_vjp(ops: Ops, wh: np.ndarray, lam: np.ndarray, beta: float, U: float, closure: Closure, C: float):
-    """Transpose of the linearised L(w) = -J(psi, w) - beta psi_x + C div(g grad w) (Eq. 1, 9), applied to lam.
-
-    wh: the spectral state at which L is linearised; lam: a physical field.
-    Returns (w_bar, C_bar): w_bar the physical field (2/3 band) L'(w)^T lam,
-    C_bar = sum over points of lam * div(g grad w) (the derivative in C).
-    """
-    a = ops.inv(ops.T * ops.fwd(lam))
+def jac_vjp(ops: Ops, wh: np.ndarray, mu: np.ndarray, U: float) -> np.ndarray:
+    """J'(w)^T mu: transpose of the linearised J(psi, w) = T F[u w_x + v w_y] (Eq. 1), physical in and out."""
+    a = ops.inv(ops.T * ops.fwd(mu))
     du, dv, dx, dy = _multipliers(ops)
     u, v = velocity(ops, wh, U)
     wx, wy = vorticity_gradient(ops, wh)
     fa = ops.fwd
-    # -J = -(u w_x + v w_y): each factor's transpose takes the other factor
-    wbar_hat = -(np.conj(du) * fa(a * wx) + np.conj(dv) * fa(a * wy) + np.conj(dx) * fa(a * u)
-                 + np.conj(dy) * fa(a * v))
-    # -beta psi_x = (i beta k_x / |k|^2) w
-    wbar_hat = wbar_hat + np.conj(1j * beta * ops.kx * ops.inv_k2) * fa(a)
+    # each factor's transpose takes the other factor
+    return ops.inv(ops.T * (np.conj(du) * fa(a * wx) + np.conj(dv) * fa(a * wy) + np.conj(dx) * fa(a * u)
+                            + np.conj(dy) * fa(a * v)))
+
+
+def sgs_vjp(ops: Ops, wh: np.ndarray, nu: np.ndarray, kind: int) -> np.ndarray:
+    """D'(w)^T nu: transpose of the linearised D(w) = T div(g grad w) (Eq. 9 without C; g of Eq. 10 or 13)."""
+    a = ops.inv(ops.T * ops.fwd(nu))
+    du, dv, dx, dy = _multipliers(ops)
+    wx, wy = vorticity_gradient(ops, wh)
+    fa = ops.fwd
+    # D = d_x(g w_x) + d_y(g w_y); p, q = the transposed derivatives of a
+    p = ops.inv(np.conj(dx) * fa(a))
+    q = ops.inv(np.conj(dy) * fa(a))
+    s = p * wx + q * wy  # the factor that multiplies the variation of g
+    if kind in (LEITH, DLEITH):
+        g = gradient_magnitude(ops, wh)
+        gx = g * p + _safe_ratio(s * wx, g)  # g = |grad w|: dg = (w_x dw_x + w_y dw_y) / g
+        gy = g * q + _safe_ratio(s * wy, g)
+        out = np.conj(dx) * fa(gx) + np.conj(dy) * fa(gy)
+    else:
+        g = strain_magnitude(ops, wh)
+        ph = -wh * ops.inv_k2
+        psi_xy = ops.inv(-(ops.kx * ops.ky) * ph)
+        psi_d = ops.inv(-(ops.kx ** 2 - ops.ky ** 2) * ph)
+        dxy = ops.kx * ops.ky * ops.inv_k2          # w -> psi_xy (real)
+        dd = (ops.kx ** 2 - ops.ky ** 2) * ops.inv_k2  # w -> psi_xx - psi_yy (real)
+        out = np.conj(dx) * fa(g * p) + np.conj(dy) * fa(g * q)
+        # |S| = sqrt(4 psi_xy^2 + psi_d^2): d|S| = (4 psi_xy dpsi_xy + psi_d dpsi_d) / |S|
+        out = out + dxy * fa(_safe_ratio(4.0 * s * psi_xy, g)) + dd * fa(_safe_ratio(s * psi_d, g))
+    return ops.inv(ops.T * out)
+
+
+def germano_vjp(ops: Ops, wh: np.ndarray, closure: Closure, U: float, C_bar: float) -> np.ndarray:
+    """C_bar times the gradient of the dynamic coefficient C(w) = max(0, <HM>/<MM>) (Eq. 11, 12, 14; R8).
+
+    Where C > 0: dC = (sum M dH + sum (H - 2 C M) dM) / (N^2 <MM>), with
+    H = J(G w) - G J(w) and M = r^p D(G w) - G D(w) (G the test filter), so
+    grad C = (H'^T M + M'^T (H - 2 C M)) / (N^2 <MM>) and
+    H'^T m = G J'(G w)^T m - J'(w)^T G m,  M'^T m = r^p G D'(G w)^T m - D'(w)^T G m.
+    Where the coefficient is clipped to 0 (or <MM> = 0) the gradient is taken as 0.
+    """
+    C, hm, mm = germano_coefficient(ops, wh, closure, U)
+    if not (C > 0.0 and mm > 0.0):
+        return np.zeros((ops.n, ops.n))
+    G = ops.test_filter(closure.test_ratio)
+    wt = G * wh
+    p = closure_power(closure.kind)
+    rp = closure.test_ratio ** p
+    H = ops.inv(jacobian_hat(ops, wt, U) - G * jacobian_hat(ops, wh, U))
+    M = ops.inv(rp * sgs_divergence_hat(ops, wt, closure.kind) - G * sgs_divergence_hat(ops, wh, closure.kind))
+
+    def Gp(f):
+        return ops.inv(G * ops.fwd(f))
+
+    nu = H - 2.0 * C * M
+    grad = (Gp(jac_vjp(ops, wt, M, U)) - jac_vjp(ops, wh, Gp(M), U)
+            + rp * Gp(sgs_vjp(ops, wt, nu, closure.kind)) - sgs_vjp(ops, wh, Gp(nu), closure.kind))
+    return C_bar * grad / (ops.n * ops.n * mm)
+
+
+def rhs_vjp(ops: Ops, wh: np.ndarray, lam: np.ndarray, beta: float, U: float, closure: Closure, C: float):
+    """Transpose of the linearised L(w) = -J(psi, w) - beta psi_x + C div(g grad w) (Eq. 1, 9), applied to lam.
+
+    wh: the spectral state at which L is linearised; lam: a physical field;
+    C: the coefficient of the static closures (the dynamic ones compute theirs
+    from wh, Eq. 12, 14, and differentiate it too).
+    Returns (w_bar, C_bar): w_bar the physical field (2/3 band) L'(w)^T lam,
+    C_bar = sum over points of lam * div(g grad w) (the derivative in C).
+    """
+    a = ops.inv(ops.T * ops.fwd(lam))
+    w_bar = -jac_vjp(ops, wh, a, U)
+    # -beta psi_x = (i beta k_x / |k|^2) w: transpose -i beta k_x / |k|^2
+    w_bar = w_bar + ops.inv(ops.T * np.conj(1j * beta * ops.kx * ops.inv_k2) * ops.fwd(a))
     C_bar = 0.0
     if closure.kind != NONE:
-        if closure.kind not in ADJOINT_CLOSURES:
-            raise ValueError("the adjoint covers closures none, Smagorinsky and Leith")
-        # div(g grad w) = d_x(g w_x) + d_y(g w_y); p, q = the transposed derivatives of a
-        p = ops.inv(np.conj(dx) * fa(a))
-        q = ops.inv(np.conj(dy) * fa(a))
-        s = p * wx + q * wy  # the factor that multiplies the variation of g
-        if closure.kind == LEITH:
-            g = gradient_magnitude(ops, wh)
-            gx = g * p + _safe_ratio(s * wx, g)  # g = |grad w|: dg = (w_x dw_x + w_y dw_y) / g
-            gy = g * q + _safe_ratio(s * wy, g)
-            wbar_hat = wbar_hat + C * (np.conj(dx) * fa(gx) + np.conj(dy) * fa(gy))
-        else:
-            g = strain_magnitude(ops, wh)
-            ph = -wh * ops.inv_k2
-            psi_xy = ops.inv(-(ops.kx * ops.ky) * ph)
-            psi_d = ops.inv(-(ops.kx ** 2 - ops.ky ** 2) * ph)
-            dxy = ops.kx * ops.ky * ops.inv_k2          # w -> psi_xy (real)
-            dd = (ops.kx ** 2 - ops.ky ** 2) * ops.inv_k2  # w -> psi_xx - psi_yy (real)
-            wbar_hat = wbar_hat + C * (np.conj(dx) * fa(g * p) + np.conj(dy) * fa(g * q))
-            # |S| = sqrt(4 psi_xy^2 + psi_d^2): d|S| = (4 psi_xy dpsi_xy + psi_d dpsi_d) / |S|
-            wbar_hat = wbar_hat + C * (dxy * fa(_safe_ratio(4.0 * s * psi_xy, g)) + dd * fa(_safe_ratio(s * psi_d, g)))
+        if closure.kind in (DSMAG, DLEITH):
+            C = germano_coefficient(ops, wh, closure, U)[0]
+        w_bar = w_bar + C * sgs_vjp(ops, wh, a, closure.kind)
         C_bar = float(np.sum(a * ops.inv(sgs_divergence_hat(ops, wh, closure.kind))))
-    return ops.inv(ops.T * wbar_hat), C_bar
+        if closure.kind in (DSMAG, DLEITH):
+            w_bar = w_bar + germano_vjp(ops, wh, closure, U, C_bar)
+    return w_bar, C_bar
 
 
 def full_step_vjp(ops: Ops, wh: np.ndarray, lam_next: np.ndarray, beta: float, U: float, closure: Closure,
@@ -111,9 +160,7 @@ def full_step_vjp(ops: Ops, wh: np.ndarray, lam_next: np.ndarray, beta: float, U
     """
     dt = params.dt
     C = 0.0
-    if closure.kind != NONE:
-        if closure.kind not in ADJOINT_CLOSURES:
-            raise ValueError("the adjoint covers closures none, Smagorinsky and Leith")
+    if closure.kind in (SMAG, LEITH):
         C = (closure.c * ops.delta) ** closure_power(closure.kind)
     # forward stages, recomputed from w_n
     stages = [wh]

@@ -99,8 +99,61 @@ def test_output_is_band_limited_with_zero_mean():
     assert np.max(np.abs(h * (1 - ops.T))) < 1e-10
 
 
-def test_dynamic_closures_are_refused():
-    n = 16
-    ops, chi, chs, wh, _, U, beta = setup(n, O.NONE, 0.0)
-    with pytest.raises(ValueError):
-        O.full_step_vjp(ops, wh, np.zeros((n, n)), beta, U, O.Closure(O.DLEITH), O.Params(), chi, chs)
+def dynamic_setup(kind, n=32):
+    """A state whose dynamic coefficient is positive (so the quotient, not the clip, is differentiated)."""
+    for seed in range(1, 40):
+        ops, chi, chs, wh, cl, U, beta = setup(n, kind, 0.0, seed=seed)
+        wh = O.project(ops, S.init_field(seed, n, L, k_peak=n / 3))
+        if O.germano_coefficient(ops, wh, cl, U)[0] > 0.0:
+            return ops, chi, chs, wh, cl, U, beta
+    raise RuntimeError("no state with a positive coefficient")
+
+
+@pytest.mark.parametrize("kind", [O.DSMAG, O.DLEITH])
+def test_germano_coefficient_gradient_matches_central_differences(kind):
+    ops, chi, chs, wh, cl, U, beta = dynamic_setup(kind)
+    grad = O.germano_vjp(ops, wh, cl, U, 1.0)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        d = ops.inv(O.project(ops, rng.standard_normal((ops.n, ops.n))))
+        eps = 1e-5
+        cp = O.germano_coefficient(ops, wh + eps * O.project(ops, d), cl, U)[0]
+        cm = O.germano_coefficient(ops, wh - eps * O.project(ops, d), cl, U)[0]
+        assert float(np.sum(grad * d)) == pytest.approx((cp - cm) / (2 * eps), rel=1e-6)
+
+
+@pytest.mark.parametrize("kind", [O.DSMAG, O.DLEITH])
+def test_dynamic_step_gradient_matches_central_differences(kind):
+    ops, chi, chs, wh, cl, U, beta = dynamic_setup(kind)
+    params = O.Params(dt=5e-3, eta=2e-2)
+    n = ops.n
+    rng = np.random.default_rng(12)
+    lam_next = rng.standard_normal((n, n))
+    lam_n, g = O.full_step_vjp(ops, wh, lam_next, beta, U, cl, params, chi, chs)
+    for _ in range(3):
+        d = ops.inv(O.project(ops, rng.standard_normal((n, n))))
+        eps = 1e-5
+        fp = loss(ops, wh + eps * O.project(ops, d), lam_next, beta, U, cl, params, chi, chs)
+        fm = loss(ops, wh - eps * O.project(ops, d), lam_next, beta, U, cl, params, chi, chs)
+        assert float(np.sum(lam_n * d)) == pytest.approx((fp - fm) / (2 * eps), rel=2e-7)
+    assert g["c"] == 0.0
+
+
+def test_clipped_dynamic_coefficient_has_no_gradient():
+    n = 32
+    for seed in range(1, 40):
+        ops, chi, chs, wh, cl, U, beta = setup(n, O.DLEITH, 0.0, seed=seed)
+        C, hm, mm = O.germano_coefficient(ops, wh, cl, U)
+        if C == 0.0 and hm < 0.0:
+            break
+    else:
+        pytest.skip("no clipped state found")
+    assert np.all(O.germano_vjp(ops, wh, cl, U, 1.0) == 0.0)
+    params = O.Params(dt=5e-3, eta=2e-2)
+    lam_next = np.random.default_rng(13).standard_normal((n, n))
+    lam_n, _ = O.full_step_vjp(ops, wh, lam_next, beta, U, cl, params, chi, chs)
+    d = ops.inv(O.project(ops, np.random.default_rng(14).standard_normal((n, n))))
+    eps = 1e-6
+    fp = loss(ops, wh + eps * O.project(ops, d), lam_next, beta, U, cl, params, chi, chs)
+    fm = loss(ops, wh - eps * O.project(ops, d), lam_next, beta, U, cl, params, chi, chs)
+    assert float(np.sum(lam_n * d)) == pytest.approx((fp - fm) / (2 * eps), rel=2e-7)
