@@ -260,9 +260,11 @@ void qg_ensemble_destroy(qg_ensemble* e);
 
 /* Discrete adjoint of one step: the vector-Jacobian product of the map
  * w_n -> w_{n+1} of the RK3 scheme (R1-R5: SSP-RK3, exact viscous factor,
- * exact Brinkman and sponge sub-steps, projection), for closures none,
- * Smagorinsky and Leith with a fixed coefficient (Eq. 10, 13).  Inner
- * products are sums over the grid points.
+ * exact Brinkman and sponge sub-steps, projection), for every closure: none,
+ * Smagorinsky and Leith with a fixed coefficient (Eq. 10, 13) and their
+ * dynamic forms, whose coefficient C = max(0, <HM>/<MM>) (Eq. 12, 14) is
+ * differentiated through the quotient (zero gradient where it is clipped).
+ * Inner products are sums over the grid points.
  *   omega_n:  N*N physical state at the start of the step (projected onto the
  *             2/3 band with zero mean first, as qg_set_state does).
  *   lam_next: N*N gradient of a loss with respect to the physical w_{n+1}
@@ -270,13 +272,15 @@ void qg_ensemble_destroy(qg_ensemble* e);
  *   lam_n:    N*N gradient with respect to the physical input field (output;
  *             2/3 band, zero mean).
  *   on_device, dtype: as for qg_set_state, for all three buffers.
- *   grads[3] or NULL: d loss / dC summed over the three stages, d loss / dc
- *             for C = (c Delta)^p, d loss / d sponge_rate.
+ *   grads[3] or NULL: d loss / dC summed over the three stages (C held
+ *             fixed), d loss / dc for C = (c Delta)^p (0 for the dynamic
+ *             closures), d loss / d sponge_rate.
  * The forward stages are recomputed from omega_n; the handle's own state and
  * stepping are untouched.  Synchronous on the handle's stream; the first call
- * allocates a workspace of 25 spectral, 37 physical and 6 mixed arrays; later
- * calls replay one captured CUDA graph.
- * QG_ERR_UNSUPPORTED for the dynamic closures and for the AB2CN scheme. */
+ * allocates a workspace of 25 spectral, 37 physical and 6 mixed arrays (39,
+ * 56 and 6 for the dynamic closures); later calls replay one captured CUDA
+ * graph.
+ * QG_ERR_UNSUPPORTED for the AB2CN scheme. */
 int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* lam_n, int32_t on_device,
                 int32_t dtype, double* grads);
 

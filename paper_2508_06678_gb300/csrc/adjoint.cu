@@ -51,11 +51,15 @@ __global__ void __launch_bounds__(kThreads) adj_combine_kernel(Geom g, AdjCombin
       re = double(o.x);
       im = double(o.y);
     }
+    const bool in_test = (long)c * c + (long)my * my <= (long)a.test_m2max;
     for (int j = 0; j < a.nterm; ++j) {
+      const int code = a.term[j].code;
+      if ((code & AM_TESTF) && !in_test) continue;
       const C x = ld<T>(a.term[j].in, e);
-      const double xr = double(x.x), xi = double(x.y), cf = a.term[j].coef;
+      const double xr = double(x.x), xi = double(x.y);
+      const double cf = a.term[j].cptr ? a.term[j].coef * a.term[j].cptr[0] : a.term[j].coef;
       double mr = 0.0, mi = 0.0;  // multiplier m = mr + i mi
-      switch (a.term[j].code) {
+      switch (code & 0xff) {
         case AM_ONE: mr = 1.0; break;
         case AM_CU: mi = -ky * ik2; break;  // conj(i k_y / |k|^2): transpose of w -> u
         case AM_CV: mi = kx * ik2; break;   // conj(-i k_x / |k|^2): transpose of w -> v
@@ -175,6 +179,22 @@ __global__ void __launch_bounds__(kThreads) adj_phys_dot_kernel(size_t count, co
     s += double(x[i]) * double(y[i]) * double(z[i]);
   s = adj_block_sum(s, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void adj_scalar_kernel(int op, const double* x0, const double* x1, const double* x2, double n2,
+                                  double* out) {
+  if (threadIdx.x != 0) return;
+  if (op == AS_COEFF) {
+    out[0] = x1[0] > 0.0 ? fmax(0.0, x0[0] / x1[0]) : 0.0;
+  } else {
+    out[0] = (x0[0] > 0.0 && x1[0] > 0.0) ? x2[0] / (n2 * x1[0]) : 0.0;
+  }
+}
+
+cudaError_t launch_adj_scalar(int op, const double* x0, const double* x1, const double* x2, double n2, double* out,
+                              cudaStream_t st) {
+  adj_scalar_kernel<<<1, 32, 0, st>>>(op, x0, x1, x2, n2, out);
+  return cudaGetLastError();
 }
 
 // out[0] = scale * sum of the partials, in a fixed order

@@ -700,6 +700,15 @@ constexpr int kAdjNP = 37;  // physical: 6 fields, 3 adjoint fields, 8 products,
 constexpr int kAdjNM = 6;   // mixed: the outputs of one derive pass
 constexpr int kAdjStageP = 19;  // first of the per-stage physical fields (u, v, w_x, w_y, psi_xy, psi_d)
 constexpr int kAdjStageS = 19;  // first of the per-stage spectral SGS fluxes F[g w_x], F[g w_y]
+// dynamic closures only: per stage the test-level state G w, H and M (spectral), G w's fields (physical),
+// scratch spectra, one physical scratch field, and four device scalars <HM>, <MM>, C, kappa per stage
+constexpr int kAdjDynS = 25;       // 3 x (G w, H, M)
+constexpr int kAdjDynTmpS = 34;    // 5 scratch spectra
+constexpr int kAdjNSDyn = 39;
+constexpr int kAdjDynP = 37;       // 3 x 6 fields of G w
+constexpr int kAdjDynMuP = 55;     // the field mu = M (or G M)
+constexpr int kAdjNPDyn = 56;
+constexpr int kAdjScalars = 8;     // offset of the per-stage scalars after the dot results
 
 int adj_alloc(qg_handle* h) {
   if (!h->adj_S.empty()) return QG_OK;
@@ -707,13 +716,14 @@ int adj_alloc(qg_handle* h) {
   const size_t spec_bytes = (size_t)h->g.Kcp * h->g.SP * csz;
   const size_t mixed_bytes = (size_t)h->g.n * h->g.IP * csz;
   const size_t phys_bytes = (size_t)h->g.n * h->g.n * h->esz;
-  std::vector<void*> S(kAdjNS), P(kAdjNP), M(kAdjNM);
+  const bool dyn = h->cl.kind == QG_DSMAG || h->cl.kind == QG_DLEITH;
+  std::vector<void*> S(dyn ? kAdjNSDyn : kAdjNS), P(dyn ? kAdjNPDyn : kAdjNP), M(kAdjNM);
   int rc = QG_OK;
   for (auto& p : S) if (!rc) rc = dalloc(h, &p, spec_bytes);
   for (auto& p : P) if (!rc) rc = dalloc(h, &p, phys_bytes);
   for (auto& p : M) if (!rc) rc = dalloc(h, &p, mixed_bytes);
   void* dots = nullptr;
-  if (!rc) rc = dalloc(h, &dots, sizeof(double) * (kAdjDotBlocks + 8));
+  if (!rc) rc = dalloc(h, &dots, sizeof(double) * (kAdjDotBlocks + kAdjScalars + 12));
   if (!rc && h->fast) {
     const int BR = h->g.n < 256 ? h->g.n : 256;
     for (void* m : M) if (!rc) rc = add_tensor_map(h, m, h->W, BR);
@@ -819,6 +829,7 @@ int adj_combine(qg_handle* h, void* out, bool accumulate, bool zero_mean,
   a.nu = h->par.nu;
   a.mu = h->par.mu;
   a.dt = h->par.dt;
+  a.test_m2max = h->test_m2max;
   Bracket br(h, QG_K_ADJ_PW);
   const cudaError_t e =
       h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream);
@@ -858,7 +869,7 @@ int adj_stage_fields(qg_handle* h, const void* Sw, int kind, int f0) {
   return adj_to_phys(h, Sw, {D_U, D_V, D_WX, D_WY}, {P[f0], P[f0 + 1], P[f0 + 2], P[f0 + 3]});
 }
 
-AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0) {
+AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0, int lam = 6) {
   auto& P = h->adj_P;
   AdjProducts a{};
   a.kind = kind;
@@ -869,7 +880,7 @@ AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0) {
   a.wy = P[f0 + 3];
   a.pxy = P[f0 + 4];
   a.pd = P[f0 + 5];
-  a.lam = P[6];
+  a.lam = P[lam];
   a.lx = P[7];
   a.ly = P[8];
   for (int k = 0; k < 8; ++k) a.out[k] = P[9 + k];
@@ -878,8 +889,60 @@ AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0) {
 
 // L(w) = -J - beta psi_x + C div(g grad w) of stage s's state Sw into spectral Sout scaled as
 // Sout = a w0 + b (ws + dt L(ws)) (Shu-Osher stage); keeps the stage's fields and SGS flux spectra
-int adj_forward_stage(qg_handle* h, int kind, double C, const void* S0, const void* Sw, void* Sout, double a,
-                      double b, int s) {
+// device scalars of stage s of a dynamic closure: <HM>, <MM>, C, kappa
+double* adj_scalar(qg_handle* h, int s, int k) { return h->adj_dots + kAdjDotBlocks + kAdjScalars + 4 * s + k; }
+
+int adj_spec_dot(qg_handle* h, const void* A, const void* B, double scale, double* out) {
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e = h->fp32 ? launch_adj_spec_dot<float>(h->g, A, B, scale, h->adj_dots, out, h->stream)
+                                : launch_adj_spec_dot<double>(h->g, A, B, scale, h->adj_dots, out, h->stream);
+  br.done();
+  CK(e, "adjoint: dot");
+  return QG_OK;
+}
+
+int adj_scalar_op(qg_handle* h, int op, const double* x0, const double* x1, const double* x2, double* out) {
+  const double n2 = double(h->g.n) * double(h->g.n);
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e = launch_adj_scalar(op, x0, x1, x2, n2, out, h->stream);
+  br.done();
+  CK(e, "adjoint: scalar");
+  return QG_OK;
+}
+
+// The dynamic coefficient of stage s (Eq. 11, 12, 14; R8) from its state Sw, recomputed with the stage:
+// G w, its fields, H = J(G w) - G J(w), M = r^p D(G w) - G D(w), <HM>, <MM>, C = max(0, <HM>/<MM>).
+// SJ holds J(w); the stage's SGS flux spectra hold F[g w_x], F[g w_y].
+int adj_forward_germano(qg_handle* h, int kind, const void* Sw, const void* SJ, int s) {
+  auto& S = h->adj_S;
+  auto& P = h->adj_P;
+  void* Swt = S[kAdjDynS + 3 * s];
+  void* SH = S[kAdjDynS + 3 * s + 1];
+  void* SM = S[kAdjDynS + 3 * s + 2];
+  const void* Sgx = S[kAdjStageS + 2 * s];
+  const void* Sgy = S[kAdjStageS + 2 * s + 1];
+  void* T0 = S[kAdjDynTmpS];
+  void* T1 = S[kAdjDynTmpS + 1];
+  void* T2 = S[kAdjDynTmpS + 2];
+  const int f0 = kAdjDynP + 6 * s;
+  const double rp = std::pow(h->cl.test_ratio, kind == AK_SMAG ? 2 : 3);
+  const double n4 = std::pow(double(h->g.n), 4);
+  int rc = adj_combine(h, Swt, false, false, {{Sw, AM_ONE | AM_TESTF, 1.0}});
+  if (!rc) rc = adj_stage_fields(h, Swt, kind, f0);
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
+  if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11]}, {T0, T1, T2});
+  if (!rc) rc = adj_combine(h, SH, false, false, {{T0, AM_ONE, 1.0}, {SJ, AM_ONE | AM_TESTF, -1.0}});
+  if (!rc)
+    rc = adj_combine(h, SM, false, false,
+                     {{T1, AM_IX, rp}, {T2, AM_IY, rp}, {Sgx, AM_IX | AM_TESTF, -1.0}, {Sgy, AM_IY | AM_TESTF, -1.0}});
+  if (!rc) rc = adj_spec_dot(h, SH, SM, 1.0 / n4, adj_scalar(h, s, 0));
+  if (!rc) rc = adj_spec_dot(h, SM, SM, 1.0 / n4, adj_scalar(h, s, 1));
+  if (!rc) rc = adj_scalar_op(h, AS_COEFF, adj_scalar(h, s, 0), adj_scalar(h, s, 1), nullptr, adj_scalar(h, s, 2));
+  return rc;
+}
+
+int adj_forward_stage(qg_handle* h, int kind, bool dyn, double C, const void* S0, const void* Sw, void* Sout,
+                      double a, double b, int s) {
   auto& S = h->adj_S;
   auto& P = h->adj_P;
   const double dt = h->par.dt;
@@ -890,18 +953,80 @@ int adj_forward_stage(qg_handle* h, int kind, double C, const void* S0, const vo
   if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
   if (!rc) rc = kind == AK_NONE ? adj_to_spec_many(h, {P[9]}, {S[8]})
                                  : adj_to_spec_many(h, {P[9], P[10], P[11]}, {S[8], Sgx, Sgy});
+  if (!rc && dyn) rc = adj_forward_germano(h, kind, Sw, S[8], s);
   if (rc) return rc;
   if (kind == AK_NONE)
     return adj_combine(h, Sout, false, false,
                        {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta}});
+  const double* cp = dyn ? adj_scalar(h, s, 2) : nullptr;
   return adj_combine(h, Sout, false, false,
                      {{S0, AM_ONE, a}, {Sw, AM_ONE, b}, {S[8], AM_ONE, -b * dt}, {Sw, AM_CV, b * dt * h->beta},
-                      {Sgx, AM_IX, b * dt * C}, {Sgy, AM_IY, b * dt * C}});
+                      {Sgx, AM_IX, b * dt * (dyn ? 1.0 : C), cp}, {Sgy, AM_IY, b * dt * (dyn ? 1.0 : C), cp}});
+}
+
+// The dynamic coefficient's share of stage s's transpose, kappa grad C (Eq. 12, 14) with kappa =
+// C_bar / (N^2 <MM>), accumulated into Slam_out:
+//   kappa [G J'(G w)^T M - J'(w)^T G M + r^p G D'(G w)^T nu - D'(w)^T G nu],  nu = H - 2 C M
+int adj_reverse_germano(qg_handle* h, int kind, void* Slam_out, int s) {
+  auto& S = h->adj_S;
+  auto& P = h->adj_P;
+  const void* SH = S[kAdjDynS + 3 * s + 1];
+  const void* SM = S[kAdjDynS + 3 * s + 2];
+  void* Snu = S[kAdjDynTmpS + 3];
+  void* Sg = S[kAdjDynTmpS + 4];
+  const double* C = adj_scalar(h, s, 2);
+  double* kappa = adj_scalar(h, s, 3);
+  const double rp = std::pow(h->cl.test_ratio, kind == AK_SMAG ? 2 : 3);
+  const int mu = kAdjDynMuP;
+  int rc = adj_scalar_op(h, AS_KAPPA, C, adj_scalar(h, s, 1), h->adj_dots + kAdjDotBlocks + s, kappa);
+  if (!rc) rc = adj_combine(h, Snu, false, false, {{SH, AM_ONE, 1.0}, {SM, AM_ONE, -2.0, C}});
+  // outer group, at the test-level state, filtered afterwards: mu = M, derivatives of nu
+  if (!rc) rc = adj_to_phys(h, SM, {D_W}, {P[mu]});
+  if (!rc) rc = adj_to_phys(h, Snu, {D_WX, D_WY}, {P[7], P[8]});
+  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjDynP + 6 * s, mu));
+  for (int pass = 0; pass < 2 && !rc; ++pass) {
+    if (pass == 1) {
+      // inner group, at the stage state: mu = G M, derivatives of G nu
+      rc = adj_combine(h, Sg, false, false, {{SM, AM_ONE | AM_TESTF, 1.0}});
+      if (!rc) rc = adj_to_phys(h, Sg, {D_W}, {P[mu]});
+      if (!rc) rc = adj_combine(h, Sg, false, false, {{Snu, AM_ONE | AM_TESTF, 1.0}});
+      if (!rc) rc = adj_to_phys(h, Sg, {D_WX, D_WY}, {P[7], P[8]});
+      if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjStageP + 6 * s, mu));
+    }
+    if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12]}, {S[8], S[9], S[10], S[11]});
+    if (!rc) rc = adj_to_spec_many(h, {P[13], P[14]}, {S[12], S[13]});
+    if (!rc && kind == AK_SMAG) rc = adj_to_spec_many(h, {P[15], P[16]}, {S[14], S[15]});
+    if (rc) return rc;
+    const int f = pass == 0 ? AM_TESTF : 0;
+    const double sj = pass == 0 ? 1.0 : -1.0, sd = pass == 0 ? rp : -1.0;
+    AdjCombine a{};
+    a.out = Slam_out;
+    a.accumulate = 1;
+    a.test_m2max = h->test_m2max;
+    auto add = [&](const void* in, int code, double coef) { a.term[a.nterm++] = AdjTerm{in, code | f, coef, kappa}; };
+    add(S[8], AM_CU, sj);
+    add(S[9], AM_CV, sj);
+    add(S[10], AM_CX, sj);
+    add(S[11], AM_CY, sj);
+    add(S[12], AM_CX, sd);
+    add(S[13], AM_CY, sd);
+    if (kind == AK_SMAG) {
+      add(S[14], AM_XY, sd);
+      add(S[15], AM_DD, sd);
+    }
+    Bracket br(h, QG_K_ADJ_PW);
+    const cudaError_t e =
+        h->fp32 ? launch_adj_combine<float>(h->g, a, h->stream) : launch_adj_combine<double>(h->g, a, h->stream);
+    br.done();
+    CK(e, "adjoint: coefficient gradient");
+  }
+  return rc;
 }
 
 // Slam_out = b lam + L'(ws)^T (b dt lam) (one Shu-Osher stage in reverse); the derivative in C,
 // b dt sum(lam * div(g grad ws)), goes to adj_dots[slot]
-int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Slam, void* Slam_out, double b, int slot) {
+int adj_reverse_stage(qg_handle* h, int kind, bool dyn, double C, const void* Slam, void* Slam_out, double b,
+                      int slot) {
   auto& S = h->adj_S;
   auto& P = h->adj_P;
   const double dt = h->par.dt, bd = b * dt;
@@ -927,11 +1052,13 @@ int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Slam, void* 
   // -beta psi_x = (i beta k_x / |k|^2) w: transpose -i beta k_x / |k|^2
   add(Slam, AM_CV, -bd * h->beta);
   if (kind != AK_NONE) {
-    add(S[12], AM_CX, bd * C);
-    add(S[13], AM_CY, bd * C);
+    const double* cp = dyn ? adj_scalar(h, slot, 2) : nullptr;
+    const double cc = dyn ? bd : bd * C;
+    a.term[a.nterm++] = AdjTerm{S[12], AM_CX, cc, cp};
+    a.term[a.nterm++] = AdjTerm{S[13], AM_CY, cc, cp};
     if (kind == AK_SMAG) {
-      add(S[14], AM_XY, bd * C);
-      add(S[15], AM_DD, bd * C);
+      a.term[a.nterm++] = AdjTerm{S[14], AM_XY, cc, cp};
+      a.term[a.nterm++] = AdjTerm{S[15], AM_DD, cc, cp};
     }
   }
   {
@@ -955,6 +1082,7 @@ int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Slam, void* 
                                               h->adj_dots + kAdjDotBlocks + slot, h->stream);
     br.done();
     CK(e, "adjoint: C derivative");
+    if (dyn) return adj_reverse_germano(h, kind, Slam_out, slot);
   }
   return QG_OK;
 }
@@ -964,15 +1092,19 @@ int adj_reverse_stage(qg_handle* h, int kind, double C, const void* Slam, void* 
 int adj_step(qg_handle* h) {
   auto& S = h->adj_S;
   auto& P = h->adj_P;
-  const int kind = h->cl.kind == QG_SMAG ? AK_SMAG : h->cl.kind == QG_LEITH ? AK_LEITH : AK_NONE;
-  const double C = kind == AK_NONE ? 0.0 : h->static_coeff;
+  const int kind = (h->cl.kind == QG_SMAG || h->cl.kind == QG_DSMAG)     ? AK_SMAG
+                   : (h->cl.kind == QG_LEITH || h->cl.kind == QG_DLEITH) ? AK_LEITH
+                                                                         : AK_NONE;
+  const bool dyn = h->cl.kind == QG_DSMAG || h->cl.kind == QG_DLEITH;
+  const double C = kind == AK_NONE || dyn ? 0.0 : h->static_coeff;
   const double dt = h->par.dt;
   double* dots = h->adj_dots + kAdjDotBlocks;
-  CK(cudaMemsetAsync(dots, 0, 8 * sizeof(double), h->stream), "adjoint: dots");
+  CK(cudaMemsetAsync(dots, 0, (kAdjScalars + 12) * sizeof(double), h->stream), "adjoint: dots");
   static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
   // forward: w0 -> w1 -> w2 -> w3 (S[0..3]), viscous factor, Brinkman -> S[4]
   int rc = adj_to_spec(h, P[17], S[0], true);
-  for (int s = 0; s < 3 && !rc; ++s) rc = adj_forward_stage(h, kind, C, S[0], S[s], S[s + 1], A[s], B[s], s);
+  for (int s = 0; s < 3 && !rc; ++s)
+    rc = adj_forward_stage(h, kind, dyn, C, S[0], S[s], S[s + 1], A[s], B[s], s);
   if (!rc) rc = adj_combine(h, S[3], false, false, {{S[3], AM_VISC, 1.0}});
   if (rc) return rc;
   if (h->fac_b) {
@@ -1019,7 +1151,7 @@ int adj_step(qg_handle* h) {
   // the three stages in reverse: w_{s+1} = a_s w0 + b_s (w_s + dt L(w_s))
   for (int s = 2; s >= 0 && !rc; --s) {
     if (A[s] != 0.0) rc = adj_combine(h, S[7], true, false, {{lam, AM_ONE, A[s]}});
-    if (!rc) rc = adj_reverse_stage(h, kind, C, lam, lam2, B[s], s);
+    if (!rc) rc = adj_reverse_stage(h, kind, dyn, C, lam, lam2, B[s], s);
     std::swap(lam, lam2);
   }
   if (!rc) rc = adj_combine(h, S[7], true, true, {{lam, AM_ONE, 1.0}});
@@ -1714,8 +1846,6 @@ int qg_step_vjp(qg_handle* h, const void* omega_n, const void* lam_next, void* l
   if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_step_vjp: bad dtype");
   if (h->scheme != QG_SCHEME_RK3_EXACT)
     return fail(QG_ERR_UNSUPPORTED, "qg_step_vjp: only the RK3 scheme has an adjoint");
-  if (h->cl.kind != QG_NONE && h->cl.kind != QG_SMAG && h->cl.kind != QG_LEITH)
-    return fail(QG_ERR_UNSUPPORTED, "qg_step_vjp: the dynamic closures have no adjoint");
   int rc = adj_alloc(h);
   if (rc) return rc;
   auto& P = h->adj_P;

@@ -38,11 +38,13 @@ enum AdjMul : int {
   AM_DD,    // (k_x^2 - k_y^2) / |k|^2   w -> psi_xx - psi_yy
   AM_VISC,  // exp(-(nu |k|^2 + mu) dt)
 };
+constexpr int AM_TESTF = 0x100;  // flag: also multiply by the test filter, |m|^2 (2r)^2 <= N^2
 constexpr int kAdjTerms = 12;
 struct AdjTerm {
-  const void* in;  // spectral array (stored band layout)
-  int code;        // AdjMul
+  const void* in;        // spectral array (stored band layout)
+  int code;              // AdjMul, optionally | AM_TESTF
   double coef;
+  const double* cptr;    // if set, coef is multiplied by this device scalar
 };
 struct AdjCombine {
   void* out;
@@ -51,7 +53,14 @@ struct AdjCombine {
   int nterm;
   AdjTerm term[kAdjTerms];
   double nu, mu, dt;  // AM_VISC
+  int test_m2max;     // AM_TESTF
 };
+// Scalar steps of the dynamic coefficient's adjoint (one thread):
+//   AS_COEFF  out = max(0, x[0] / x[1]) if x[1] > 0 else 0          (C from <HM>, <MM>, Eq. 12, 14)
+//   AS_KAPPA  out = x[2] / (n2 x[1]) if x[0] > 0 and x[1] > 0 else 0  (C_bar / (N^2 <MM>); x = C, <MM>, C_bar)
+enum AdjScalarOp : int { AS_COEFF = 0, AS_KAPPA = 1 };
+cudaError_t launch_adj_scalar(int op, const double* x0, const double* x1, const double* x2, double n2, double* out,
+                              cudaStream_t st);
 enum AdjKind : int { AK_NONE = 0, AK_SMAG = 1, AK_LEITH = 2 };
 enum AdjProdMode : int { AP_FORWARD = 0, AP_ADJOINT = 1 };
 // Pointwise products (physical arrays, working precision).

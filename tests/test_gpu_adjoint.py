@@ -105,12 +105,40 @@ def test_device_buffers_match_host_and_leave_the_state_alone():
     assert np.array_equal(solver.get_state(), ref.get_state())
 
 
+def positive_coefficient_state(n, kind):
+    """A state whose dynamic coefficient is positive (the quotient, not the clip, is differentiated)."""
+    ops = O.Ops(n, L)
+    for seed in range(1, 60):
+        w = S.init_field(seed, n, L, k_peak=n / 3)
+        if O.germano_coefficient(ops, O.project(ops, w), O.Closure(kind), 0.5)[0] > 0.0:
+            return w
+    raise RuntimeError("no state with a positive coefficient")
+
+
+@pytest.mark.parametrize("n,kind", [(48, O.DSMAG), (54, O.DLEITH), (256, O.DLEITH), (256, O.DSMAG)])
+def test_dynamic_step_vjp_matches_the_oracle_fp64(n, kind):
+    solver, ops, chi, chs, params, cl, beta, U = make(n, kind, 0.0)
+    w = positive_coefficient_state(n, kind)
+    lam_next = np.random.default_rng(n + kind).standard_normal((n, n))
+    got, g = solver.step_vjp(w, lam_next)
+    ref, gr = O.full_step_vjp(ops, O.project(ops, w), lam_next, beta, U, cl, params, chi, chs)
+    assert rel(got, ref) < 1e-10
+    assert g["C"] == pytest.approx(gr["C"], rel=1e-9)
+    assert g["sponge_rate"] == pytest.approx(gr["sponge_rate"], rel=1e-9)
+    assert g["c"] == 0.0
+
+
+def test_dynamic_step_vjp_fp32():
+    n, kind = 256, O.DLEITH
+    solver, ops, chi, chs, params, cl, beta, U = make(n, kind, 0.0, precision=qg.QG_FP32)
+    w = positive_coefficient_state(n, kind)
+    lam_next = np.random.default_rng(3).standard_normal((n, n))
+    got, _ = solver.step_vjp(w.astype(np.float32), lam_next.astype(np.float32))
+    ref, _ = O.full_step_vjp(ops, O.project(ops, w), lam_next, beta, U, cl, params, chi, chs)
+    assert rel(got.astype(np.float64), ref) < 1e-4
+
+
 def test_unsupported_configurations_are_refused():
-    for kind in (O.DSMAG, O.DLEITH):
-        solver, *_ = make(48, kind, 0.0)
-        with pytest.raises(qg.QGError) as e:
-            solver.step_vjp(np.zeros((48, 48)), np.zeros((48, 48)))
-        assert e.value.code == qg.QG_ERR_UNSUPPORTED
     s = qg.QGSolver(48, kind=O.SMAG, c=0.2, scheme=qg.QG_SCHEME_AB2CN, eta=1e-2)
     with pytest.raises(qg.QGError) as e:
         s.step_vjp(np.zeros((48, 48)), np.zeros((48, 48)))
