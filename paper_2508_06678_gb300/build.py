@@ -44,7 +44,7 @@ def build(verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
         return r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, len(srcs), os.cpu_count() or 8)) as ex:
         for msg in ex.map(compile_one, zip(srcs, objs)):
             if verbose and msg:
                 print(msg, file=sys.stderr)

@@ -1,5 +1,5 @@
-// Register-resident FFT engine and the specialised row / column passes for
-// power-of-two grids (256 <= N <= 4096).
+// Register-resident FFT engines and the specialised row / column passes for
+// grids N = 2^p (256 <= N <= 4096, engine E16) and N = 3 * 2^p (384 <= N <= 3072, engine E12).
 //
 // Engine (E16): a length-N sequence is owned by TT = N/16 threads; thread t
 // holds the 16 elements at natural positions t + TT*m (m = 0..15).  A
@@ -64,15 +64,68 @@ template <typename C> __device__ __forceinline__ void dft16(C* v, int s) {
   }
 }
 
+// 3-point DFT with kernel exp(s 2 pi i n k / 3)
+template <typename C> __device__ __forceinline__ void dft3(C* v, int s) {
+  using T = decltype(C::x);
+  const T h = T(0.86602540378443864676);  // sin(pi/3)
+  const C a = v[0];
+  const C bc = cadd(v[1], v[2]);
+  const C d = csub(v[1], v[2]);
+  const C m = mk<C>(a.x - T(0.5) * bc.x, a.y - T(0.5) * bc.y);
+  const C r = cmul_si(cscale(d, h), s);  // i s sin(pi/3) (v1 - v2)
+  v[0] = cadd(a, bc);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+
+// 12-point DFT as 4 x 3: n = 3 n1 + n2, k = k1 + 4 k2; 4-point DFTs over n1, twiddles
+// exp(s 2 pi i n2 k1 / 12), 3-point DFTs over n2
+template <typename C> __device__ __forceinline__ void dft12(C* v, int s) {
+  using T = decltype(C::x);
+  const T h = T(0.86602540378443864676);  // cos(pi/6) = sin(pi/3)
+  const T ss = T(s);
+  C a[3][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    C q[4] = {v[n2], v[3 + n2], v[6 + n2], v[9 + n2]};
+    dft4(q, s);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = q[k1];
+  }
+  a[1][1] = cmulk(a[1][1], h, ss * T(0.5));    // 30 degrees
+  a[1][2] = cmulk(a[1][2], T(0.5), ss * h);    // 60
+  a[1][3] = cmul_si(a[1][3], s);               // 90
+  a[2][1] = cmulk(a[2][1], T(0.5), ss * h);    // 60
+  a[2][2] = cmulk(a[2][2], T(-0.5), ss * h);   // 120
+  a[2][3] = mk<C>(-a[2][3].x, -a[2][3].y);     // 180
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C q[3] = {a[0][k1], a[1][k1], a[2][k1]};
+    dft3(q, s);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) v[k1 + 4 * k2] = q[k2];
+  }
+}
+
 template <typename C, int R> __device__ __forceinline__ void dftR(C* v, int s) {
   if constexpr (R == 16) dft16(v, s);
+  else if constexpr (R == 12) dft12(v, s);
   else if constexpr (R == 8) dft8(v, s);
   else if constexpr (R == 4) dft4(v, s);
+  else if constexpr (R == 3) dft3(v, s);
   else dft2(v);
+}
+
+// grid sizes with register-resident kernels: 2^p (16 elements per thread) and 3 * 2^p (12)
+constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+constexpr int elems_per_thread(int n) { return is_pow2(n) ? 16 : 12; }
+constexpr bool fast_size(int n) {
+  return (is_pow2(n) && n >= 256 && n <= 4096) || (n % 3 == 0 && is_pow2(n / 3) && n >= 384 && n <= 3072);
 }
 
 template <typename T, int N> struct E16 {
   using C = cplx_t<T>;
+  static constexpr int EL = 16;
   static constexpr int TT = N / 16;
   static constexpr int LOG2N = ilog2(N);
   static constexpr int NP16 = LOG2N / 4;
@@ -158,7 +211,95 @@ template <typename T, int N> struct E16 {
   }
 };
 
+// Engine E12 for N = 3 * 2^j (384 <= N <= 3072): a length-N sequence is owned by TT = N/12 threads, thread t
+// holding the 12 elements t + TT*m (m = 0..11).  The passes are Stockham DIT passes as in E16: radix 12
+// first (as 4 x 3), then radix 4 while a factor 4 remains, then radix 2 for odd j.  A radix-R pass takes
+// 12/R butterflies per thread, each reading the thread's own elements (N/R is a multiple of TT), and the
+// last pass lands on natural ownership again.  Twiddle tables per pass as in E16: [r - 1][k], k = j mod NS.
+template <typename T, int N> struct E12 {
+  using C = cplx_t<T>;
+  static constexpr int EL = 12;
+  static constexpr int TT = N / 12;
+  static constexpr int J = ilog2(N / 12);
+  static constexpr int NP4 = J / 2;                 // radix-4 passes after the radix-12 one
+  static constexpr int RLAST = (J % 2) ? 2 : 1;     // a final radix-2 pass for odd J
+  static constexpr int BUF = N + N / 16;
+  static constexpr int K = (N - 1) / 3;
+  static constexpr int Kc = K + 1;
+  static_assert(N % 12 == 0 && is_pow2(N / 12) && N >= 384 && N <= 3072, "E12 engine: N must be 3 * 2^p, 384..3072");
+
+  __device__ static __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+  // span of radix-4 pass p (1-based) and its table offset; the radix-2 pass follows at span N / 2
+  static constexpr int ns4(int p) { return p <= 1 ? 12 : 4 * ns4(p - 1); }
+  static constexpr int off4(int p) { return p <= 1 ? 0 : off4(p - 1) + 3 * ns4(p - 1); }
+
+  template <int R, int NS, bool LAST, int OFF>
+  __device__ static __forceinline__ void pass(C* x, int t, C* buf, const C* __restrict__ ptw, int sign) {
+    constexpr int NB = 12 / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + TT * b;
+      const int k = j % NS;
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = x[b + NB * r];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = __ldg(&ptw[OFF + (r - 1) * NS + k]);
+          if (sign > 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dftR<C, R>(v, sign);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b + NB * r] = v[r];
+      } else {
+        const int base_i = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad(base_i + NS * r)] = v[r];
+      }
+    }
+    if constexpr (!LAST) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 12; ++m) x[m] = buf[pad(t + TT * m)];
+    }
+  }
+
+  template <int P>
+  __device__ static __forceinline__ void run4(C* x, int t, C* b0, C* b1, int& ph, const C* __restrict__ ptw,
+                                              int sign) {
+    if constexpr (P <= NP4) {
+      constexpr bool last = (P == NP4 && RLAST == 1);
+      pass<4, ns4(P), last, off4(P)>(x, t, ph ? b1 : b0, ptw, sign);
+      if (!last) ph ^= 1;
+      run4<P + 1>(x, t, b0, b1, ph, ptw, sign);
+    }
+  }
+
+  __device__ static __forceinline__ void run(C* x, int t, C* b0, C* b1, int& ph, const C* __restrict__ ptw,
+                                             int sign) {
+    pass<12, 1, false, 0>(x, t, ph ? b1 : b0, ptw, sign);
+    ph ^= 1;
+    run4<1>(x, t, b0, b1, ph, ptw, sign);
+    if constexpr (RLAST == 2) pass<2, N / 2, true, off4(NP4 + 1)>(x, t, ph ? b1 : b0, ptw, sign);
+  }
+};
+
+template <typename T, int N> struct EngineOf { using type = E16<T, N>; };
+template <typename T> struct EngineOf<T, 384> { using type = E12<T, 384>; };
+template <typename T> struct EngineOf<T, 768> { using type = E12<T, 768>; };
+template <typename T> struct EngineOf<T, 1536> { using type = E12<T, 1536>; };
+template <typename T> struct EngineOf<T, 3072> { using type = E12<T, 3072>; };
+template <typename T, int N> using Eng = typename EngineOf<T, N>::type;
+
 }  // namespace fast
+
+// rows of one TMA box of the specialised column pass (a divisor of N)
+constexpr int fast_box_rows(int n) { return n < 256 ? n : (n % 256 == 0 ? 256 : 128); }
 
 // k_x columns per CTA of the specialised column pass
 template <int N> int fast_col_width();

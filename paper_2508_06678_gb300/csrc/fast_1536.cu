@@ -1,0 +1,6 @@
+// Specialised passes for N = 1536 (3 * 2^p, engine E12); see fast_kernels.cuh.
+#include "fast_kernels.cuh"
+
+namespace qg {
+QG_INSTANTIATE_FAST(1536)
+}  // namespace qg

@@ -1,4 +1,4 @@
-// Specialised row / column passes for power-of-two N on the E16 engine.
+// Specialised row / column passes on the register-resident engines (E16 for N = 2^p, E12 for N = 3 * 2^p).
 // Same arithmetic and data layouts as row.cu / column.cu (see there for the
 // equations); only the FFT organisation differs.  Included by fast_<N>.cu,
 // one translation unit per grid size.
@@ -28,7 +28,7 @@ namespace qg {
 namespace fast {
 
 template <int N> struct RowCfg {
-  static constexpr int TT = N / 16;
+  static constexpr int TT = N / elems_per_thread(N);
   static constexpr int ROWS = TT >= 128 ? 1 : 128 / TT;
   static constexpr int THREADS = TT * ROWS;
 };
@@ -47,11 +47,11 @@ template <int OP> struct Occ<double, OP> { static constexpr int row = 1, col = 1
 #endif
 template <int N> struct ColCfg {
   static constexpr int W = QG_COL_W;  // k_x columns per CTA
-  static constexpr int TT = N / 16;
+  static constexpr int TT = N / elems_per_thread(N);
   static constexpr int THREADS = W * TT;
   // column stride in shared memory (complex elements): 16 / W mod 16 keeps the exchanges conflict-free
   static constexpr int CP = N + N / 16 + 16 / W;
-  static constexpr int BR = N < 256 ? N : 256;  // rows per TMA box
+  static constexpr int BR = fast_box_rows(N);  // rows per TMA box
   static constexpr int NBOX = N / BR;
 };
 // bytes of one shared-memory stage: a dense W x N tile for TMA, or W padded exchange columns
@@ -84,7 +84,7 @@ __device__ __forceinline__ void smag_p(T u, T v, T wx, T wy, T pxy, T pd, T& J, 
 // ---------------------------------------------------------------------------
 template <typename T, int N>
 struct RowCtx {
-  using E = E16<T, N>;
+  using E = Eng<T, N>;
   using C = cplx_t<T>;
   static constexpr int TT = E::TT;
   int t, y;
@@ -100,7 +100,7 @@ struct RowCtx {
     const C* A = reinterpret_cast<const C*>(Av) + (size_t)y * g->IP;
     const C* B = Bv ? reinterpret_cast<const C*>(Bv) + (size_t)y * g->IP : nullptr;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       const int k = t + TT * m;
       C z = mk<C>(T(0), T(0));
       if (k <= E::K) {
@@ -127,19 +127,19 @@ struct RowCtx {
     C* ub = ph ? b1 : b0;
     ph ^= 1;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) ub[E::pad(t + TT * m)] = x[m];
+    for (int m = 0; m < E::EL; ++m) ub[E::pad(t + TT * m)] = x[m];
     __syncthreads();
     C* A = reinterpret_cast<C*>(Av) + (size_t)y * g->IP;
     C* B = Bv ? reinterpret_cast<C*>(Bv) + (size_t)y * g->IP : nullptr;
     const T ks = T(g->kscale);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       const int k = t + TT * m;
       if (k < g->Kcp) {
         C a = mk<C>(T(0), T(0)), b = mk<C>(T(0), T(0));
         if (k < E::Kc) {
           const C z = x[m];
-          const C zm = ub[E::pad((N - k) & (N - 1))];
+          const C zm = ub[E::pad(k == 0 ? 0 : N - k)];
           a = mk<C>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
           b = mk<C>(T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x));
           const T kx = ks * T(k);
@@ -154,7 +154,7 @@ struct RowCtx {
 
   __device__ __forceinline__ void check(const T* v) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) bad |= !isfinite(v[m]);
+    for (int m = 0; m < E::EL; ++m) bad |= !isfinite(v[m]);
   }
 };
 
@@ -165,18 +165,19 @@ template <typename T, int N, bool SMAG, bool NONE>
 __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, const void* const* in, T* J, T* P,
                                                T* Q) {
   using C = cplx_t<T>;
+  using E = Eng<T, N>;
   cx.inv_pair(x, in[0], in[1]);
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < E::EL; ++m) {
     J[m] = x[m].x;  // u_total
     P[m] = x[m].y;  // v
   }
   cx.inv_pair(x, in[2], in[3]);  // (w_x, w_y)
   if constexpr (SMAG) {
-    C s[16];
+    C s[E::EL];
     cx.inv_pair(s, in[4], in[5]);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       T j, p, q;
       smag_p<T>(J[m], P[m], x[m].x, x[m].y, s[m].x, s[m].y, j, p, q);
       J[m] = j;
@@ -185,10 +186,10 @@ __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, c
     }
   } else if constexpr (NONE) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) J[m] = J[m] * x[m].x + P[m] * x[m].y;
+    for (int m = 0; m < E::EL; ++m) J[m] = J[m] * x[m].x + P[m] * x[m].y;
   } else {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       T j, p, q;
       leith_p<T>(J[m], P[m], x[m].x, x[m].y, j, p, q);
       J[m] = j;
@@ -206,7 +207,7 @@ __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, c
 template <typename T, int N, int PROG>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kernel(Geom g, RowDesc d,
                                                                        const cplx_t<T>* __restrict__ tw) {
-  using E = E16<T, N>;
+  using E = Eng<T, N>;
   using C = cplx_t<T>;
   constexpr int TT = E::TT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -226,38 +227,38 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
   }
   const int t = cx.t;
   const size_t yN = (size_t)cx.y * N;
-  C x[16];
+  C x[E::EL];
 
   if constexpr (PROG == RP_NONE || PROG == RP_LEITH || PROG == RP_SMAG || PROG == RP_DLEITH || PROG == RP_DSMAG) {
     constexpr bool smag = PROG == RP_SMAG || PROG == RP_DSMAG;
     constexpr bool dyn = PROG == RP_DLEITH || PROG == RP_DSMAG;
     constexpr bool none = PROG == RP_NONE;
     constexpr int per = smag ? 6 : 4;  // inputs per level
-    T J[16], P[16], Q[16];
+    T J[E::EL], P[E::EL], Q[E::EL];
     level_products<T, N, smag, none>(cx, x, d.in + 0, J, P, Q);
     if constexpr (none) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], T(0));
+      for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(J[m], T(0));
       cx.fwd_store(x, d.out[0], nullptr, false, false);
     } else {
       // outputs: 0 J, 1 P (times i k_x), 2 Q [, 3 J~, 4 P~ (times i k_x), 5 Q~]
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], P[m]);
+      for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(J[m], P[m]);
       cx.fwd_store(x, d.out[0], d.out[1], false, true);
       if constexpr (!dyn) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) x[m] = mk<C>(Q[m], T(0));
+        for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(Q[m], T(0));
         cx.fwd_store(x, d.out[2], nullptr, false, false);
       } else {
-        T Qk[16];
+        T Qk[E::EL];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) Qk[m] = Q[m];
+        for (int m = 0; m < E::EL; ++m) Qk[m] = Q[m];
         level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) x[m] = mk<C>(Qk[m], Q[m]);
+        for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(Qk[m], Q[m]);
         cx.fwd_store(x, d.out[2], d.out[5], false, false);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) x[m] = mk<C>(J[m], P[m]);
+        for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(J[m], P[m]);
         cx.fwd_store(x, d.out[3], d.out[4], false, true);
       }
     }
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
     const T* fac = reinterpret_cast<const T*>(d.factor) + yN;
     cx.inv_pair(x, d.in[0], d.nin > 1 ? d.in[1] : nullptr);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       const T f = fac[t + TT * m];
       x[m] = mk<C>(x[m].x * f, x[m].y * f);
       cx.bad |= !isfinite(x[m].x) | !isfinite(x[m].y);
@@ -277,17 +278,17 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
       const T* src = reinterpret_cast<const T*>(d.phys_in) + yN;
       const T* src2 = d.phys_in2 ? reinterpret_cast<const T*>(d.phys_in2) + yN : nullptr;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = mk<C>(src[t + TT * m], src2 ? src2[t + TT * m] : T(0));
+      for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(src[t + TT * m], src2 ? src2[t + TT * m] : T(0));
       cx.fwd_store(x, d.out[0], src2 ? d.out[1] : nullptr, false, false);
     } else {
       cx.inv_pair(x, d.in[0], d.phys_out2 ? d.in[1] : nullptr);
       T* dst = reinterpret_cast<T*>(d.phys_out) + yN;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) dst[t + TT * m] = x[m].x;
+      for (int m = 0; m < E::EL; ++m) dst[t + TT * m] = x[m].x;
       if (d.phys_out2) {
         T* dst2 = reinterpret_cast<T*>(d.phys_out2) + yN;
 #pragma unroll
-        for (int m = 0; m < 16; ++m) dst2[t + TT * m] = x[m].y;
+        for (int m = 0; m < E::EL; ++m) dst2[t + TT * m] = x[m].y;
       }
     }
   }
@@ -320,7 +321,7 @@ constexpr int kStateBatch = QG_STATE_BATCH;
 template <typename T, int N, int OP>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(
     Geom g, ColDesc d, const cplx_t<T>* __restrict__ tw, const __grid_constant__ TmaSet tm) {
-  using E = E16<T, N>;
+  using E = Eng<T, N>;
   using C = cplx_t<T>;
   constexpr int W = ColCfg<N>::W;
   constexpr int TT = E::TT;
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   C* dh = reinterpret_cast<C*>(d.dh);
   const size_t colbase = (size_t)mx * g.SP;
 
-  C x[16], A[16], B[16];
+  C x[E::EL], A[E::EL], B[E::EL];
   GermanoAcc<T> acc_hm, acc_mm;
 
   // ---- forward y-transforms (k values land in natural ownership: k = t + TT m)
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
         return;
       }
 #pragma unroll
-      for (int m = 0; m < 16; ++m) x[m] = st[(t + TT * m) * W + c];
+      for (int m = 0; m < E::EL; ++m) x[m] = st[(t + TT * m) * W + c];
       ph = 0;
       E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, -1);
       // every thread is done with this stage: hand it to the TMA for field f + 2
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
                        2 * c0, bx * BR, &mbar[sidx]);
       }
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 0; m < E::EL; ++m) {
         const int k = t + TT * m;
         const int my = k <= K ? k : k - N;
         const T ky = T(g.kscale) * T(my);
@@ -528,9 +529,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
     const C* bhp = reinterpret_cast<const C*>(d.bh);
     C* ep = reinterpret_cast<C*>(d.eprev);
     C* wsp = reinterpret_cast<C*>(d.wss);
-    constexpr int GB = kStateBatch;
+    constexpr int GB = E::EL % kStateBatch == 0 ? kStateBatch : 4;  // a divisor of the thread's elements
+    static_assert(E::EL % GB == 0, "state batch must divide the elements per thread");
 #pragma unroll
-    for (int m0 = 0; m0 < 16; m0 += GB) {
+    for (int m0 = 0; m0 < E::EL; m0 += GB) {
       // per op: u0 = w^n (or w* in the AB2CN final), u1 = stage field or E_prev,
       // u2 = J, u3 = D, u4 = Brinkman forcing, u5 = previous w*; vf = viscous factor
       C u0[GB], u1[GB], u2[GB], u3[GB], u4[GB], u5[GB];
@@ -648,10 +650,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
     // return physical values), 1/|k|^2, and masks of the kept 2/3 band and of
     // the test filter; each derived field then costs a few operations per mode.
     const T scale = T(1.0 / n2);
-    T ik2[16];
+    T ik2[E::EL];
     unsigned keep = 0u, intest = 0u;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
+    for (int m = 0; m < E::EL; ++m) {
       const int k = t + TT * m;
       const int my = k <= K ? k : k - N;
       const int m2 = mx * mx + my * my;
@@ -668,42 +670,42 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
       // test-filtered fields vanish for k_x beyond the test band: their arrays stay zero there
       if ((code & D_TEST) && c0 > d.test_kmax) continue;
       const unsigned on = (code & D_TEST) ? (keep & intest) : keep;
-      C w[16];
+      C w[E::EL];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) w[m] = ((on >> m) & 1u) ? A[m] : mk<C>(T(0), T(0));
+      for (int m = 0; m < E::EL; ++m) w[m] = ((on >> m) & 1u) ? A[m] : mk<C>(T(0), T(0));
 #define QG_KY(m) (ksc * T((t + TT * (m)) <= K ? (t + TT * (m)) : (t + TT * (m)) - N))
       switch (code & 7) {
         case D_U:  // -i ky psi, psi = -w / |k|^2
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(cscale(w[m], ik2[m]), QG_KY(m));
+          for (int m = 0; m < E::EL; ++m) x[m] = cmul_ik(cscale(w[m], ik2[m]), QG_KY(m));
           if (mx == 0 && t == 0) x[0] = mk<C>(T(d.U), T(0));
           break;
         case D_V:  // i kx psi
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(cscale(w[m], -ik2[m]), kxv);
+          for (int m = 0; m < E::EL; ++m) x[m] = cmul_ik(cscale(w[m], -ik2[m]), kxv);
           break;
         case D_WX:
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(w[m], kxv);
+          for (int m = 0; m < E::EL; ++m) x[m] = cmul_ik(w[m], kxv);
           break;
         case D_WY:
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = cmul_ik(w[m], QG_KY(m));
+          for (int m = 0; m < E::EL; ++m) x[m] = cmul_ik(w[m], QG_KY(m));
           break;
         case D_PXY:  // -kx ky psi = kx ky w / |k|^2
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = cscale(w[m], kxv * QG_KY(m) * ik2[m]);
+          for (int m = 0; m < E::EL; ++m) x[m] = cscale(w[m], kxv * QG_KY(m) * ik2[m]);
           break;
         case D_PD:  // -(kx^2 - ky^2) psi = (kx^2 - ky^2) w / |k|^2
 #pragma unroll
-          for (int m = 0; m < 16; ++m) {
+          for (int m = 0; m < E::EL; ++m) {
             const T ky = QG_KY(m);
             x[m] = cscale(w[m], (kxv * kxv - ky * ky) * ik2[m]);
           }
           break;
         default:
 #pragma unroll
-          for (int m = 0; m < 16; ++m) x[m] = w[m];
+          for (int m = 0; m < E::EL; ++m) x[m] = w[m];
           break;
       }
 #undef QG_KY
@@ -716,7 +718,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
       E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, +1);
       __syncthreads();  // all exchange reads of the stage are done
 #pragma unroll
-      for (int m = 0; m < 16; ++m) st[(t + TT * m) * W + c] = x[m];
+      for (int m = 0; m < E::EL; ++m) st[(t + TT * m) * W + c] = x[m];
       tma::fence_proxy_async();
       __syncthreads();
       if (lead) {
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
 
 template <typename T, int N>
 cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cudaStream_t st) {
-  using E = fast::E16<T, N>;
+  using E = fast::Eng<T, N>;
   using Cfg = fast::RowCfg<N>;
   const size_t smem = (size_t)2 * Cfg::ROWS * E::BUF * sizeof(cplx_t<T>);
   const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);

@@ -124,11 +124,24 @@ namespace qg {
 // Non-first passes of the specialised FFT in order (radix-16 passes, then the
 // last pass of radix 2^(log2 n mod 4)); each contributes (R - 1) * NS entries
 // [r - 1][k] = W_n^(r k n / (NS R)).
+// The twiddled passes (every pass after the first) of the specialised engines, in order:
+// N = 2^p: radix 16 while possible, then one radix-8/4/2 pass; N = 3 * 2^p: radix 4 after the first
+// (radix-12) pass while a factor 4 remains, then one radix-2 pass for odd p.
 static void for_each_pass(int n, void (*fn)(int, int, int, void*), void* ctx) {
+  int off = 0;
+  if (n % 3 == 0) {
+    int m = n / 12, ns = 12;
+    for (; m >= 4; m /= 4, ns *= 4) {
+      fn(4, ns, off, ctx);
+      off += 3 * ns;
+    }
+    if (m == 2) fn(2, ns, off, ctx);
+    return;
+  }
   int lg = 0;
   while ((1 << lg) < n) ++lg;
   const int np16 = lg / 4, rlast = 1 << (lg % 4);
-  int off = 0, ns = 16;
+  int ns = 16;
   for (int p = 1; p < np16; ++p, ns *= 16) {
     fn(16, ns, off, ctx);
     off += 15 * ns;
@@ -354,6 +367,10 @@ cudaError_t row_fast_dispatch(qg_handle* h, const RowDesc& d) {
     case 1024: return launch_row_fast<T, 1024>(h->g, d, h->ptw, h->stream);
     case 2048: return launch_row_fast<T, 2048>(h->g, d, h->ptw, h->stream);
     case 4096: return launch_row_fast<T, 4096>(h->g, d, h->ptw, h->stream);
+    case 384: return launch_row_fast<T, 384>(h->g, d, h->ptw, h->stream);
+    case 768: return launch_row_fast<T, 768>(h->g, d, h->ptw, h->stream);
+    case 1536: return launch_row_fast<T, 1536>(h->g, d, h->ptw, h->stream);
+    case 3072: return launch_row_fast<T, 3072>(h->g, d, h->ptw, h->stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -378,6 +395,10 @@ cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
     case 1024: return launch_col_fast<T, 1024>(h->g, d, h->ptw, tm, h->stream);
     case 2048: return launch_col_fast<T, 2048>(h->g, d, h->ptw, tm, h->stream);
     case 4096: return launch_col_fast<T, 4096>(h->g, d, h->ptw, tm, h->stream);
+    case 384: return launch_col_fast<T, 384>(h->g, d, h->ptw, tm, h->stream);
+    case 768: return launch_col_fast<T, 768>(h->g, d, h->ptw, tm, h->stream);
+    case 1536: return launch_col_fast<T, 1536>(h->g, d, h->ptw, tm, h->stream);
+    case 3072: return launch_col_fast<T, 3072>(h->g, d, h->ptw, tm, h->stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -725,7 +746,7 @@ int adj_alloc(qg_handle* h) {
   void* dots = nullptr;
   if (!rc) rc = dalloc(h, &dots, sizeof(double) * (kAdjDotBlocks + kAdjScalars + 12));
   if (!rc && h->fast) {
-    const int BR = h->g.n < 256 ? h->g.n : 256;
+    const int BR = fast_box_rows(h->g.n);
     for (void* m : M) if (!rc) rc = add_tensor_map(h, m, h->W, BR);
   }
   if (rc) return rc;
@@ -1415,9 +1436,9 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     return fail(QG_ERR_UNSUPPORTED, "qg_create: row pass needs %zu B of shared memory (n=%d, closure %d)",
                 h->row_smem, n, closure->kind);
   }
-  // power-of-two grids use the register-resident kernels (two k_x columns per CTA)
+  // 2^p and 3 * 2^p grids use the register-resident kernels (two k_x columns per CTA)
   {
-    const bool pow2 = (n & (n - 1)) == 0 && n >= 256 && n <= 4096;
+    const bool spec = fast::fast_size(n);
     int fw = 2;
     switch (n) {
       case 256: fw = fast_col_width<256>(); break;
@@ -1425,11 +1446,17 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
       case 1024: fw = fast_col_width<1024>(); break;
       case 2048: fw = fast_col_width<2048>(); break;
       case 4096: fw = fast_col_width<4096>(); break;
+      case 384: fw = fast_col_width<384>(); break;
+      case 768: fw = fast_col_width<768>(); break;
+      case 1536: fw = fast_col_width<1536>(); break;
+      case 3072: fw = fast_col_width<3072>(); break;
     }
     const size_t dense = (size_t)n * fw * csz, padded = (size_t)fw * (n + n / 16 + 16 / fw) * csz;
     const size_t fast_col_smem = 3 * (((dense > padded ? dense : padded) + 1023) / 1024 * 1024) + 1024;
-    const size_t fast_row_smem = (size_t)2 * (n >= 2048 ? 1 : 2048 / n) * (n + n / 16) * csz;
-    h->fast = pow2 && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
+    const int tt = spec ? n / fast::elems_per_thread(n) : 1;
+    const int rows = tt >= 128 ? 1 : 128 / tt;  // rows per CTA of the row pass
+    const size_t fast_row_smem = (size_t)2 * rows * (n + n / 16) * csz;
+    h->fast = spec && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
     if (getenv("QG_FORCE_GENERIC")) h->fast = false;
     if (h->fast) h->W = fw;
   }
@@ -1500,7 +1527,7 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   }
   // tensor maps of every mixed array for the TMA column pass
   if (h->fast) {
-    const int BR = n < 256 ? n : 256;
+    const int BR = fast_box_rows(n);
     for (int i = 0; i < kMaxIn; ++i)
       if (h->X[i] && (rc = add_tensor_map(h, h->X[i], h->W, BR))) { delete h; return rc; }
     for (int i = 0; i < kMaxY; ++i)

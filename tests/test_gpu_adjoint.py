@@ -192,3 +192,13 @@ def test_autograd_rollout_mse_loss():
     ref, _ = oracle_rollout_grad(ops, w0.detach().cpu().numpy(), nsteps, obs, beta, U, cl, params, chi, chs)
     assert rel(w0.grad.cpu().numpy(), ref) < 1e-9
     assert set(solver.param_grads) == {"C", "c", "sponge_rate"}
+
+
+def test_step_vjp_on_a_three_times_power_of_two_grid():
+    solver, ops, chi, chs, params, cl, beta, U = make(384, O.LEITH, 0.5)
+    w = S.init_field(3, 384, L, k_peak=40)
+    lam_next = np.random.default_rng(5).standard_normal((384, 384))
+    got, g = solver.step_vjp(w, lam_next)
+    ref, gr = O.full_step_vjp(ops, O.project(ops, w), lam_next, beta, U, cl, params, chi, chs)
+    assert rel(got, ref) < 1e-10
+    assert g["c"] == pytest.approx(gr["c"], rel=1e-9)

@@ -51,7 +51,7 @@ def make_pair(n, kind, *, geometry="island", beta=5.0, U=0.5, c=0.2, radius=0.8,
     return ref, gpu, w0
 
 
-@pytest.mark.parametrize("n", [16, 18, 24, 48, 54, 96, 128, 256, 384, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("n", [16, 18, 24, 48, 54, 96, 128, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096])
 @pytest.mark.parametrize("prec,tol", [(qg.QG_FP64, 1e-13), (qg.QG_FP32, 2e-6)])
 def test_projection_round_trip(n, prec, tol):
     """set_state/get_state = forward then inverse 2-D transform with the 2/3 band (Sec. II-C)."""
@@ -79,9 +79,9 @@ def test_one_step_parity_fp64(kind, n):
 
 
 @pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
-@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("n", [128, 256, 384])
 def test_100_step_parity_fp64_island(kind, n):
-    """128^2 runs the generic kernels, 256^2 the register-resident power-of-two kernels."""
+    """128^2 runs the generic kernels, 256^2 the register-resident 2^p kernels, 384^2 the 3 * 2^p ones."""
     ref, gpu, _ = make_pair(n, kind, radius=0.4, seed=0, k_peak=16.0)
     ref.step(100)
     gpu.step(100)
@@ -202,9 +202,10 @@ def test_full_size_production_step_fp32():
 
 @pytest.mark.parametrize("kind", [S.SMAG, S.DLEITH])
 @pytest.mark.parametrize("prec,tol", [(qg.QG_FP64, 1e-12), (qg.QG_FP32, 2e-5)])
-def test_fast_and_generic_kernels_agree(kind, prec, tol, monkeypatch):
-    """The power-of-two kernels and the generic mixed-radix kernels compute the same step."""
-    n = 512
+@pytest.mark.parametrize("n", [512, 384, 768])
+def test_fast_and_generic_kernels_agree(kind, prec, tol, n, monkeypatch):
+    """The register-resident kernels (2^p and 3 * 2^p engines) and the generic mixed-radix kernels compute the
+    same step."""
     wl = S.Workload("t", n, "island", beta=5.0, U=0.5, closure=kind, c=0.2, radius=0.6, seed=7)
     w0 = S.init_field(7, n, k_peak=40.0)
     out = []
@@ -312,7 +313,7 @@ def test_full_size_fp32_error_against_fp64_100_steps():
         assert abs(a - b) < 5e-3 * abs(b)
 
 
-@pytest.mark.parametrize("n,prec", [(256, qg.QG_FP32), (96, qg.QG_FP64), (2048, qg.QG_FP32)])
+@pytest.mark.parametrize("n,prec", [(256, qg.QG_FP32), (96, qg.QG_FP64), (2048, qg.QG_FP32), (768, qg.QG_FP32)])
 def test_graph_replay_is_bitwise_eager(n, prec, monkeypatch):
     """qg_step replays one captured step as a CUDA graph on a capturable stream;
     the result is bit-identical to launching the same kernels one by one."""
