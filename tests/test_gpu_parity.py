@@ -313,6 +313,46 @@ def test_full_size_fp32_error_against_fp64_100_steps():
         assert abs(a - b) < 5e-3 * abs(b)
 
 
+def test_island128_smagorinsky_200_steps_fp64_against_the_oracle():
+    """The small FP64 configuration in full: 128^2 island, Smagorinsky c_S = 0.17, 200 steps."""
+    wl = S.island128_smag()
+    ref = O.QGOracle(wl.n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure, c=wl.c),
+                     O.Params(dt=wl.dt, nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate))
+    ref.set_state(wl.omega0())
+    ref.step(wl.steps)
+    with qg.QGSolver.from_workload(wl, precision=qg.QG_FP64) as s:
+        s.set_state(wl.omega0())
+        s.step(wl.steps)
+        got = s.get_state()
+        d = s.diagnostics()
+    assert rel(got, ref.get_state()) < 1e-11
+    r = ref.diagnostics()
+    assert d["energy"] == pytest.approx(r["energy"], rel=1e-11)
+    assert d["enstrophy"] == pytest.approx(r["enstrophy"], rel=1e-11)
+
+
+@pytest.mark.parametrize("kind", [S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+def test_cape512_2000_steps_fp32_energy_and_enstrophy_within_half_percent(kind):
+    """Long runs of the closure sweep (512^2 cape, beta = 10, U = 1, 2000 steps): the FP32 form's energy and
+    enstrophy stay within 0.5% of the FP64 form's (which the oracle pins), every 500 steps."""
+    wl = S.cape512(kind)
+    w0 = wl.omega0()
+    solvers = {p: qg.QGSolver.from_workload(wl, precision=p) for p in (qg.QG_FP64, qg.QG_FP32)}
+    for s in solvers.values():
+        s.set_state(w0)
+    for _ in range(4):
+        diag = {}
+        for p, s in solvers.items():
+            s.step(500)
+            diag[p] = s.diagnostics()
+        for key in ("energy", "enstrophy"):
+            a, b = diag[qg.QG_FP32][key], diag[qg.QG_FP64][key]
+            assert abs(a - b) < 5e-3 * abs(b), (key, a, b)
+        assert diag[qg.QG_FP32]["finite"]
+    for s in solvers.values():
+        s.close()
+
+
 @pytest.mark.parametrize("n,prec", [(256, qg.QG_FP32), (96, qg.QG_FP64), (2048, qg.QG_FP32), (768, qg.QG_FP32)])
 def test_graph_replay_is_bitwise_eager(n, prec, monkeypatch):
     """qg_step replays one captured step as a CUDA graph on a capturable stream;
