@@ -76,3 +76,12 @@ def test_series_pair_count_matches_the_oracle_nan_pattern():
     ff = np.zeros((7, 2))
     dist, _ = O.lag_table(les, ff, -3, 4)
     assert bench.valid_pairs(5, 7, -3, 4) == int(np.sum(~np.isnan(dist)))
+
+
+def test_ensemble_shards_partition_the_members():
+    for world in (1, 2, 3, 4, 8):
+        shards = [bench.ensemble_shard(96, r, world) for r in range(world)]
+        flat = sorted(i for sh in shards for i in sh)
+        assert flat == list(range(96))
+        sizes = [len(sh) for sh in shards]
+        assert max(sizes) - min(sizes) <= 1
