@@ -208,6 +208,145 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+class TorchFFTStep:
+    """The same RK3 step (readings R1-R5) written with torch.fft (cuFFT) and torch elementwise ops, FP32 on the
+    GPU, eager: a library-FFT implementation of the method, timed beside libqg as context only.
+
+    Sec. II-A Eq. 1 with the closures of Eq. 9-14, the exact Brinkman (Eq. 2) and sponge (Eq. 3) sub-steps and the
+    2/3 rule, in numpy's rfft2 layout.  The dynamic coefficient stays on the device (no host round trip).
+    """
+
+    def __init__(self, wl, dtype=None, device="cuda"):
+        import torch
+        self.torch = torch
+        dev = device
+        self.dtype = dtype or torch.float32
+        n, L = wl.n, wl.L
+        self.n, self.wl = n, wl
+        mx = torch.arange(n // 2 + 1, device=dev, dtype=torch.float64)[None, :]
+        my = torch.fft.fftfreq(n, 1.0 / n, device=dev, dtype=torch.float64)[:, None]
+        sc = 2 * math.pi / L
+        kx, ky = sc * mx, sc * my
+        k2 = kx ** 2 + ky ** 2
+        inv_k2 = torch.where(k2 > 0, 1.0 / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+        K = (n - 1) // 3
+        T = ((mx.abs() <= K) & (my.abs() <= K)).to(torch.float64)
+        G = ((mx ** 2 + my ** 2) * (2.0 * wl.test_ratio) ** 2 <= float(n) ** 2).to(torch.float64)
+        rd = self.dtype
+        self.kx = kx.to(rd)
+        self.ky = ky.to(rd)
+        self.inv_k2 = inv_k2.to(rd)
+        self.T = T.to(rd)
+        self.G = G.to(rd)
+        self.visc = torch.exp(-(wl.nu * k2 + wl.mu) * wl.dt).to(rd)
+        self.fb = torch.exp(torch.from_numpy(-wl.mask() * wl.dt / wl.eta)).to(dev, rd) if wl.geometry != "none" else None
+        sp = wl.sponge_field()
+        self.fs = torch.exp(torch.from_numpy(-wl.sponge_rate * sp * wl.dt)).to(dev, rd) if sp is not None else None
+        self.delta = L / n
+
+    def inv(self, fh):
+        return self.torch.fft.irfft2(fh, s=(self.n, self.n))
+
+    def fwd(self, f):
+        return self.torch.fft.rfft2(f)
+
+    def project(self, w):
+        wh = self.T * self.fwd(w.to(self.dtype))
+        wh[0, 0] = 0
+        return wh
+
+    def velocity(self, wh):
+        ph = -wh * self.inv_k2
+        return self.inv(-1j * self.ky * ph) + self.wl.U, self.inv(1j * self.kx * ph)
+
+    def grad(self, wh):
+        return self.inv(1j * self.kx * wh), self.inv(1j * self.ky * wh)
+
+    def jac(self, wh):
+        u, v = self.velocity(wh)
+        wx, wy = self.grad(wh)
+        return self.T * self.fwd(u * wx + v * wy)
+
+    def eddy(self, wh, smag):
+        if smag:
+            ph = -wh * self.inv_k2
+            pxy = self.inv(-(self.kx * self.ky) * ph)
+            pd = self.inv(-(self.kx ** 2 - self.ky ** 2) * ph)
+            return self.torch.sqrt(4 * pxy * pxy + pd * pd)
+        wx, wy = self.grad(wh)
+        return self.torch.sqrt(wx * wx + wy * wy)
+
+    def sgs(self, wh, smag):
+        g = self.eddy(wh, smag)
+        wx, wy = self.grad(wh)
+        return self.T * (1j * self.kx * self.fwd(g * wx) + 1j * self.ky * self.fwd(g * wy))
+
+    def rhs(self, wh):
+        wl = self.wl
+        out = -self.jac(wh) - wl.beta * (1j * self.kx * (-wh * self.inv_k2))
+        if wl.closure == S.NONE:
+            return out
+        smag = wl.closure in (S.SMAG, S.DSMAG)
+        D = self.sgs(wh, smag)
+        if wl.closure in (S.SMAG, S.LEITH):
+            C = (wl.c * self.delta) ** (2 if smag else 3)
+        else:
+            wt = self.G * wh
+            H = self.inv(self.jac(wt) - self.G * self.jac(wh))
+            M = self.inv(wl.test_ratio ** (2 if smag else 3) * self.sgs(wt, smag) - self.G * D)
+            hm, mm = (H * M).mean(), (M * M).mean()
+            C = self.torch.where(mm > 0, self.torch.clamp(hm / self.torch.where(mm > 0, mm, self.torch.ones_like(mm)),
+                                                          min=0), self.torch.zeros_like(mm))
+        return out + C * D
+
+    def step(self, wh):
+        dt = self.wl.dt
+        w0, ws = wh, wh
+        for a, b in ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)):
+            ws = a * w0 + b * (ws + dt * self.rhs(ws))
+        w = self.visc * ws
+        if self.fb is not None:
+            u, v = self.velocity(w)
+            w = self.T * (1j * self.kx * self.fwd(self.fb * v) - 1j * self.ky * self.fwd(self.fb * u))
+        if self.fs is not None:
+            w = self.T * self.fwd(self.fs * self.inv(w))
+        w = self.T * w
+        w[0, 0] = 0
+        return w
+
+
+def torch_fft_context(wl, ours_ms: float, steps: int = 20):
+    """Time the torch.fft form of the step and compare its field with libqg's after 20 steps (FP32 both)."""
+    import torch
+    import paper_2508_06678_gb300 as qg
+    ts = TorchFFTStep(wl)
+    w0 = wl.omega0()
+    wh = ts.project(torch.from_numpy(w0).cuda())
+    for _ in range(3):
+        wh = ts.step(wh)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        wh = ts.step(wh)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    wh = ts.project(torch.from_numpy(w0).cuda())
+    for _ in range(20):
+        wh = ts.step(wh)
+    a = ts.inv(wh).double().cpu().numpy()
+    with qg.QGSolver.from_workload(wl, precision=qg.QG_FP32) as s:
+        s.set_state(w0)
+        s.step(20)
+        b = s.get_state()
+    return {"ms_per_step": ms, "value": wl.n * wl.n / (ms / 1e3), "unit": UNIT, "libqg_speedup": ms / ours_ms,
+            "rel_l2_diff_vs_libqg_after_20_steps": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+            "what": "the same RK3 step in eager torch (torch.fft rfft2/irfft2 = cuFFT, elementwise torch ops), FP32, "
+                    f"{steps} steps after 3 warm-up"}
+
+
 def time_oracle(wl, max_seconds: float, warmup: int = 1, scheme: int = 0):
     """The FP64 CPU oracle, as it stands, on the workload; bounded wall time."""
     import oracle as O
@@ -873,6 +1012,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 throughput / error leg")
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--err-steps", type=int, default=100)
+    ap.add_argument("--no-torch-context", action="store_true",
+                    help="skip timing the torch.fft (cuFFT) form of the step beside libqg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         raise SystemExit("--warmup must be >= 3")
@@ -1045,6 +1186,10 @@ def main():
                 "energy_rel_diff": abs(d32["energy"] - d64["energy"]) / abs(d64["energy"]),
                 "enstrophy_rel_diff": abs(d32["enstrophy"] - d64["enstrophy"]) / abs(d64["enstrophy"])}
 
+    torch_ctx = None
+    if rank == 0 and scheme == 0 and fp32 and not args.no_torch_context:
+        torch_ctx = torch_fft_context(wl, ms / args.steps)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -1064,6 +1209,7 @@ def main():
                        "l2": "working set > 126 MB L2 (inputs larger than L2, no flush)",
                        "final_energy": diag["energy"], "final_coeff": diag["coeff"], "finite": diag["finite"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
+            "torch_fft_context": torch_ctx,
             "kernel_ms": {k: v[1] for k, v in per_class.items() if v[0]},
             "kernel_launches": {k: v[0] for k, v in per_class.items() if v[0]},
             "clocks": clocks,

@@ -85,3 +85,22 @@ def test_ensemble_shards_partition_the_members():
         assert flat == list(range(96))
         sizes = [len(sh) for sh in shards]
         assert max(sizes) - min(sizes) <= 1
+
+
+@pytest.mark.parametrize("kind", [S.NONE, S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+def test_torch_fft_context_step_is_the_oracle_step(kind):
+    """The torch.fft form timed beside libqg computes the oracle's step (run here on the CPU in FP64)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    wl = S.Workload("t", 48, "island", beta=5.0, U=0.5, closure=kind, c=0.2, radius=0.8, seed=1)
+    ts = bench.TorchFFTStep(wl, dtype=torch.float64, device="cpu")
+    w0 = S.init_field(1, 48, k_peak=16)
+    wh = ts.project(torch.from_numpy(w0))
+    ref = O.QGOracle(48, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(kind, c=0.2), O.Params())
+    ref.set_state(w0)
+    for _ in range(5):
+        wh = ts.step(wh)
+    ref.step(5)
+    a, b = ts.inv(wh).numpy(), ref.get_state()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-12
