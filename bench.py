@@ -396,10 +396,11 @@ def run_reference(args, wl):
 SERIES = {"n": 512, "nsnap": 96, "lag": 32, "seed": 21, "dt_snap": 0.1, "shift": 3}
 SERIES_METRIC = "pair-points/s of the Eq. 15-16 lag table, 512^2 FP32 series, 96 snapshots, lags -32..32"
 SERIES_UNIT = "pair-points/s"
-# FP32-pipe instructions per (pair, point) in the pairs kernel: the difference
-# and its compensated square (1 + 10), the two centred values and their
-# compensated product (2 + 10)
-SERIES_INST = 23
+# FP32 operations per (pair, point) of the plain definition of the two sums:
+# a - b and its square added (one FMA), a - a_mean, b - b_mean and their
+# product added (one FMA); the FP32-pipe roofline counts these, whatever the
+# kernel spends on top (compensation, shared centring)
+SERIES_INST = 5
 
 
 def series_inputs():

@@ -47,7 +47,7 @@ extern "C" {
 #define QG_ERR_CUDA (-2)      /* a CUDA runtime call failed (message has the CUDA error) */
 #define QG_ERR_NONFINITE (-3) /* a non-finite value appeared in the state; stepping stopped */
 #define QG_ERR_OOM (-4)       /* device allocation failed */
-#define QG_ERR_TIMEOUT (-5)   /* reserved: a bounded device wait gave up */
+#define QG_ERR_TIMEOUT (-5)   /* a bounded device wait gave up (an async copy never arrived) */
 #define QG_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve (e.g. shared memory) */
 
 /* Working precision of the device fields. */
@@ -206,9 +206,12 @@ int qg_grid_filter(const double* omega_fr, int32_t nsnap, int32_t n_fr, int32_t 
  *        groups (moments, pairs, finish, phase), from CUDA events recorded
  *        on stream around them (-1 where an event could not be made).
  * QG_ERR_ARG if no lag in the range pairs two snapshots.  FP32 series are
- * differenced and multiplied in FP32 with each thread's sums compensated,
- * chunk sums and all means in FP64; FP64 series run in FP64.  Deterministic;
- * synchronous; allocates its scratch per call. */
+ * differenced and multiplied in FP32, summed in short FMA chains that join
+ * compensated per-thread totals, chunk sums and all means in FP64; FP64
+ * series run in FP64.  Deterministic; synchronous.  Scratch (and the device
+ * copy of host series) comes stream-ordered from a memory pool the library
+ * keeps per device; the pool holds freed blocks for later calls until the
+ * process ends. */
 int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32_t n_ff_snap, int64_t npts,
                       int32_t dtype, int32_t on_device, int32_t lag_min, int32_t lag_max, void* stream, double* dist,
                       double* pcc, double* mean_dist, int32_t* phase, double* kernel_ms);

@@ -8,19 +8,26 @@
 // negative lag).
 //
 // Kernels (all reductions in a fixed order, so results are deterministic):
-//   moments   (chunk, snapshot) CTAs: chunk sums, then chunk sums of squares
-//             about the mean (compensated per thread for FP32 fields)
-//   pairs     a 16 x 16 tile of (t, phi) pairs per CTA, one pair per thread,
-//             over one chunk of the points; the 16 ff rows and the 31 les
-//             rows the tile needs are staged through shared memory (rows
-//             padded by one element so the up to 17 distinct rows a warp
-//             reads fall in distinct banks); FP32 series keep each thread's
-//             sums compensated (TwoProduct / TwoSum), FP64 partials per chunk
-//   finish    the chunks' partials summed per pair; PCC from the moments
-//   phase     mean distance per lag and its argmin (one CTA)
+//   moments   (snapshot, slice) CTAs: each slice's sum, then its sum of
+//             squares about its own mean (compensated per thread for FP32
+//             fields); norm: the slices merged per snapshot in FP64 (mean,
+//             1 / sqrt of the centred sum of squares)
+//   pairs     a 16 x 16 tile of (t, phi) pairs per CTA of 64 threads, a 2 x 2
+//             block of pairs per thread (two snapshots 8 apart, two lags 8
+//             apart: three distinct les rows), over one chunk of the points;
+//             the 16 ff rows and the 31 les rows the tile needs are staged
+//             through shared memory and read 16 bytes at a time; sums run in
+//             short FMA chains folded into compensated (TwoSum) totals for
+//             FP32 series, FP64 partials per chunk
+//   finish    the chunks' partials summed per pair (a warp per pair, fixed
+//             order); PCC from the moments
+//   phase     mean distance per lag (a warp per lag) and, in the last CTA to
+//             finish, its argmin
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "../../include/qg.h"
@@ -39,8 +46,6 @@ constexpr int kMaxLag = 1 << 16;
 constexpr size_t kMaxPairs = size_t(1) << 24;
 constexpr size_t kPartialBytes = size_t(256) << 20;
 
-template <typename T> struct Stage { static constexpr int P = 128; };  // points staged per round
-template <> struct Stage<double> { static constexpr int P = 64; };     // same shared-memory bytes
 
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -55,18 +60,53 @@ __device__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// Per-snapshot moments in two passes over a grid of (chunk, snapshot) CTAs,
-// snapshots 0 .. n_a - 1 from series a and the rest from series b.
-// Pass 1 writes each chunk's sum; pass 2 forms the mean from those sums (a
-// fixed-order warp reduction, identical in every CTA of the snapshot) and
-// writes each chunk's sum of (x - m_c)^2 about the mean rounded to the
-// working precision, m_c.  Per-thread sums are compensated for FP32 fields.
+// The 16-byte vector a thread reads from a staged row, and its lanes.
+template <typename T> struct Vec;
+template <> struct Vec<float> { static constexpr int W = 4; };
+template <> struct Vec<double> { static constexpr int W = 2; };
+
+template <typename T, int W>
+__device__ __forceinline__ void load_lanes(const T* p, T (&x)[W]) {
+  if constexpr (W == 4 && sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+  } else if constexpr (W == 2 && sizeof(T) == 8) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    x[0] = v.x, x[1] = v.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < W; ++i) x[i] = p[i];
+  }
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void store_lanes(T* p, const T (&x)[W]) {
+  if constexpr (W == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else if constexpr (W == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < W; ++i) p[i] = x[i];
+  }
+}
+
+// Per-snapshot moments over a grid of (snapshot, slice) CTAs, snapshots
+// 0 .. n_a - 1 from series a and the rest from series b.  Each CTA reads its
+// slice twice (the second time from L2: the resident slices fit in it): the
+// slice's sum, then the sum of (x - m_s)^2 about the slice's own mean rounded
+// to the working precision, m_s.  Per-thread sums are compensated for FP32
+// fields.  The norm kernel then merges the slices exactly in FP64: the mean,
+// and the centred sum of squares
+//   M2 = sum_s [ sq_s - n_s (mu_s - m_s)^2 + n_s (mu_s - mean)^2 ],
+// mu_s = sum_s / n_s (the pairwise-variance update of Chan, Golub and LeVeque).
 struct MomArgs {
   int n_a, nsnap, nchunk;
   int64_t npts, chunk;
-  double* sum_part;  // [snap][chunk]
-  double* sq_part;   // [snap][chunk]
+  double* sum_part;  // [snap][slice]: sum of the slice
+  double* sq_part;   // [snap][slice]: sum of (x - m_s)^2 about the slice's mean in the working precision
   double* mean;      // [snap]
+  double* rnorm;     // [snap]: 1 / sqrt(M2), 0 for a constant field
 };
 
 template <typename T>
@@ -87,55 +127,56 @@ template <> struct SumAcc<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) series_sum_kernel(const T* __restrict__ a, const T* __restrict__ b,
-                                                              MomArgs A) {
+__global__ void __launch_bounds__(kThreads) series_moments_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                                                  MomArgs A) {
   __shared__ double red[kThreads / 32];
+  __shared__ double m_sh;
   const int snap = blockIdx.x;
   const T* f = snapshot(a, b, A, snap);
   const int64_t p0 = (int64_t)blockIdx.y * A.chunk;
   const int64_t p1 = p0 + A.chunk < A.npts ? p0 + A.chunk : A.npts;
   SumAcc<T> acc;
   for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) acc.add(f[p]);
-  const double v = block_sum(acc.value(), red);
-  if (threadIdx.x == 0) A.sum_part[(size_t)snap * A.nchunk + blockIdx.y] = v;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) series_sq_kernel(const T* __restrict__ a, const T* __restrict__ b,
-                                                             MomArgs A) {
-  __shared__ double red[kThreads / 32];
-  __shared__ double m_sh;
-  const int snap = blockIdx.x;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < A.nchunk; c += 32) s += A.sum_part[(size_t)snap * A.nchunk + c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) {
-      m_sh = s / double(A.npts);
-      if (blockIdx.y == 0) A.mean[snap] = m_sh;
-    }
+  const double s = block_sum(acc.value(), red);
+  if (threadIdx.x == 0) {
+    A.sum_part[(size_t)snap * A.nchunk + blockIdx.y] = s;
+    m_sh = s / double(p1 - p0);
   }
   __syncthreads();
   const T mc = T(m_sh);
-  const T* f = snapshot(a, b, A, snap);
-  const int64_t p0 = (int64_t)blockIdx.y * A.chunk;
-  const int64_t p1 = p0 + A.chunk < A.npts ? p0 + A.chunk : A.npts;
-  GermanoAcc<T> acc;
+  GermanoAcc<T> q;
   for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
     const T d = f[p] - mc;
-    acc.add_prod(d, d);
+    q.add_prod(d, d);
   }
-  const double v = block_sum(acc.value(), red);
+  const double v = block_sum(q.value(), red);
   if (threadIdx.x == 0) A.sq_part[(size_t)snap * A.nchunk + blockIdx.y] = v;
 }
 
-// centred sum of squares of one snapshot: the chunks' sums about m_c, less n (m - m_c)^2
-__device__ double snapshot_css(const MomArgs& M, int snap, int fp32) {
+// one warp per snapshot: the slices merged in a fixed order
+constexpr int kNormThreads = 256;
+__global__ void __launch_bounds__(kNormThreads) series_norm_kernel(MomArgs A, int fp32) {
+  const int snap = blockIdx.x * (kNormThreads / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (snap >= A.nsnap) return;
+  const double* sp = A.sum_part + (size_t)snap * A.nchunk;
+  const double* qp = A.sq_part + (size_t)snap * A.nchunk;
+  double s = 0.0;
+  for (int c = lane; c < A.nchunk; c += 32) s += sp[c];
+  for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  const double mean = s / double(A.npts);
   double q = 0.0;
-  for (int c = 0; c < M.nchunk; ++c) q += M.sq_part[(size_t)snap * M.nchunk + c];
-  const double m = M.mean[snap];
-  const double mc = fp32 ? double(float(m)) : m;
-  return q - double(M.npts) * (m - mc) * (m - mc);
+  for (int c = lane; c < A.nchunk; c += 32) {
+    const int64_t p0 = (int64_t)c * A.chunk;
+    const double n = double((p0 + A.chunk < A.npts ? p0 + A.chunk : A.npts) - p0);
+    const double mu = sp[c] / n;  // the moments kernel's slice mean, bit for bit
+    const double m = fp32 ? double(float(mu)) : mu;
+    q += qp[c] - n * (mu - m) * (mu - m) + n * (mu - mean) * (mu - mean);
+  }
+  for (int m = 16; m > 0; m >>= 1) q += __shfl_xor_sync(0xffffffffu, q, m);
+  if (lane == 0) {
+    A.mean[snap] = mean;
+    A.rnorm[snap] = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+  }
 }
 
 struct PairArgs {
@@ -143,56 +184,168 @@ struct PairArgs {
   int64_t npts, chunk;
   const double* mean_les;
   const double* mean_ff;
-  double* part;  // [chunk][t][j][2]: sum (a - b)^2, sum (a - a_c)(b - b_c)
+  double* part;  // [t][j][chunk][2]: sum (a - b)^2, sum (a - a_c)(b - b_c)
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) series_pairs_kernel(const T* __restrict__ les, const T* __restrict__ ff,
-                                                                PairArgs A) {
-  constexpr int P = Stage<T>::P;
-  __shared__ T sa[kRowsA][P + 1];
-  __shared__ T sb[kTileT][P + 1];
-  const int i = threadIdx.x / kTileL, j = threadIdx.x % kTileL;
+// One thread's four pairs at W consecutive points.  rows: les rows ra - 8, ra,
+// ra + 8 and ff rows ti, ti + 8 of the tile; c: their centres.  Pair k = 2u + v
+// (snapshot t + 8u, lag j + 8v) reads les row ra + 8(u - v) and ff row ti + 8u.
+// cd / cc: per-lane chains of sum (a - b)^2 and sum (a - a_c)(b - b_c).
+template <typename T, int W>
+__device__ __forceinline__ void pair_terms(const T* const (&rows)[5], int p, const T (&c)[5], T (&cd)[4][W],
+                                           T (&cc)[4][W]) {
+  T x[5][W];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) load_lanes<T, W>(rows[r] + p, x[r]);
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const T a_m = x[0][w], a_0 = x[1][w], a_p = x[2][w], b_0 = x[3][w], b_8 = x[4][w];
+    const T ca_m = a_m - c[0], ca_0 = a_0 - c[1], ca_p = a_p - c[2], cb_0 = b_0 - c[3], cb_8 = b_8 - c[4];
+    T d = a_0 - b_0;
+    cd[0][w] = fma(d, d, cd[0][w]);
+    cc[0][w] = fma(ca_0, cb_0, cc[0][w]);
+    d = a_m - b_0;
+    cd[1][w] = fma(d, d, cd[1][w]);
+    cc[1][w] = fma(ca_m, cb_0, cc[1][w]);
+    d = a_p - b_8;
+    cd[2][w] = fma(d, d, cd[2][w]);
+    cc[2][w] = fma(ca_p, cb_8, cc[2][w]);
+    d = a_0 - b_8;
+    cd[3][w] = fma(d, d, cd[3][w]);
+    cc[3][w] = fma(ca_0, cb_8, cc[3][w]);
+  }
+}
+
+// the chains of one block summed as a balanced tree, added to the running totals
+template <typename T, int W>
+__device__ __forceinline__ void fold(T (&cd)[4][W], T (&cc)[4][W], SumAcc<T> (&td)[4], SumAcc<T> (&tc)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T sd, sc;
+    if constexpr (W == 4) {
+      sd = (cd[k][0] + cd[k][1]) + (cd[k][2] + cd[k][3]);
+      sc = (cc[k][0] + cc[k][1]) + (cc[k][2] + cc[k][3]);
+    } else if constexpr (W == 2) {
+      sd = cd[k][0] + cd[k][1];
+      sc = cc[k][0] + cc[k][1];
+    } else {
+      sd = cd[k][0];
+      sc = cc[k][0];
+    }
+    td[k].add(sd);
+    tc[k].add(sc);
+#pragma unroll
+    for (int w = 0; w < W; ++w) cd[k][w] = T(0), cc[k][w] = T(0);
+  }
+}
+
+// A 16 x 16 tile of (t, phi) pairs per CTA of 64 threads; thread (ti, li)
+// takes snapshots t0 + ti + {0, 8} and lags j0 + li + {0, 8}, whose four les
+// snapshots are three rows of the staged tile.  Each round stages the 31 les
+// rows and the 16 ff rows of P points (rows padded by 16 bytes: the 8 les rows
+// a quarter warp reads with one 16-byte load each start 16 bytes apart modulo
+// 128 bytes and fall in distinct banks), then each thread adds its pairs'
+// terms in blocks of kFold vectors: plain FMA chains, one per vector lane,
+// whose tree sum joins a compensated running total (TwoSum for FP32; a block
+// sum carries at most (kFold + 2) u relative rounding of its terms).
+// kVec (rows start on 16-byte boundaries): the rows are staged with 16-byte
+// loads and stores; otherwise element by element.
+constexpr int kPairW = 8;
+constexpr int kPairThreads = kPairW * kPairW;
+constexpr int kFold = 4;
+constexpr int kRowsStaged = kRowsA + kTileT;  // les rows, then ff rows
+constexpr int kStageBytes = 512;              // bytes of a staged row per round
+static_assert(2 * kPairW == kTileT && 2 * kPairW == kTileL, "a thread takes two snapshots and two lags");
+
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(kPairThreads) series_pairs_kernel(const T* __restrict__ les,
+                                                                    const T* __restrict__ ff, PairArgs A) {
+  constexpr int W = Vec<T>::W;
+  constexpr int P = kStageBytes / int(sizeof(T));  // points per round
+  constexpr int LD = P + W;                         // padded row length in elements
+  constexpr int NQ = P / W;                         // vectors per staged row
+  __shared__ __align__(16) T stage[kRowsStaged * LD];
+  const int ti = threadIdx.x / kPairW, li = threadIdx.x % kPairW;
   const int t0 = blockIdx.y * kTileT, j0 = blockIdx.z * kTileL;
-  const int t = t0 + i, jl = j0 + j;
-  const int s = t - (A.lag_min + jl);                     // les snapshot of this pair
   const int s_row0 = t0 - A.lag_min - j0 - (kTileL - 1);  // les snapshot of staged row 0
-  const bool valid = t < A.n_ff && jl < A.nlag && s >= 0 && s < A.n_les;
-  if (!__syncthreads_or(valid)) return;  // no pair of this tile exists
-  // centres of the cross sum in the working precision (the finish kernel corrects for their rounding)
-  const T am = valid ? T(A.mean_les[s]) : T(0);
-  const T bm = valid ? T(A.mean_ff[t]) : T(0);
-  GermanoAcc<T> d2, cr;
-  const int ra = i - j + kTileL - 1;
+  const int ra = ti - li + kTileL - 1;                     // les row of pairs (t, j) and (t + 8, j + 8)
+  bool valid[4];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int t = t0 + ti + kPairW * (k >> 1), jl = j0 + li + kPairW * (k & 1);
+    const int s = t - (A.lag_min + jl);
+    valid[k] = t < A.n_ff && jl < A.nlag && s >= 0 && s < A.n_les;
+    any = any || valid[k];
+  }
+  if (!__syncthreads_or(any)) return;  // no pair of this tile exists
+  // centres in the working precision (the finish kernel corrects for their rounding)
+  T c[5];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int sn = s_row0 + ra + kPairW * (r - 1);
+    c[r] = (sn >= 0 && sn < A.n_les) ? T(A.mean_les[sn]) : T(0);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int tn = t0 + ti + kPairW * u;
+    c[3 + u] = tn < A.n_ff ? T(A.mean_ff[tn]) : T(0);
+  }
+  const T* const rows[5] = {stage + (ra - kPairW) * LD, stage + ra * LD, stage + (ra + kPairW) * LD,
+                            stage + (kRowsA + ti) * LD, stage + (kRowsA + ti + kPairW) * LD};
+  SumAcc<T> td[4], tc[4];
+  T cd[4][W] = {}, cc[4][W] = {};
   const int64_t p_begin = (int64_t)blockIdx.x * A.chunk;
   const int64_t p_end = p_begin + A.chunk < A.npts ? p_begin + A.chunk : A.npts;
   for (int64_t p0 = p_begin; p0 < p_end; p0 += P) {
     const int np = p_end - p0 < P ? int(p_end - p0) : P;
     __syncthreads();  // the previous round's reads are done
-    for (int e = threadIdx.x; e < kRowsA * P; e += kThreads) {
-      const int r = e / P, p = e - r * P;
-      const int sn = s_row0 + r;
-      sa[r][p] = (p < np && sn >= 0 && sn < A.n_les) ? les[(size_t)sn * (size_t)A.npts + (size_t)(p0 + p)] : T(0);
-    }
-    for (int e = threadIdx.x; e < kTileT * P; e += kThreads) {
-      const int r = e / P, p = e - r * P;
-      const int tn = t0 + r;
-      sb[r][p] = (p < np && tn < A.n_ff) ? ff[(size_t)tn * (size_t)A.npts + (size_t)(p0 + p)] : T(0);
+    if constexpr (kVec) {  // np is a whole number of vectors
+      for (int e = threadIdx.x; e < kRowsStaged * NQ; e += kPairThreads) {
+        const int r = e / NQ, q = e - r * NQ;
+        const bool is_les = r < kRowsA;
+        const int sn = is_les ? s_row0 + r : t0 + r - kRowsA;
+        const bool in = q * W < np && sn >= 0 && sn < (is_les ? A.n_les : A.n_ff);
+        T x[W] = {};
+        if (in) load_lanes<T, W>((is_les ? les : ff) + (size_t)sn * (size_t)A.npts + (size_t)(p0 + q * W), x);
+        store_lanes<T, W>(stage + r * LD + q * W, x);
+      }
+    } else {
+      for (int e = threadIdx.x; e < kRowsStaged * P; e += kPairThreads) {
+        const int r = e / P, p = e - r * P;
+        const bool is_les = r < kRowsA;
+        const int sn = is_les ? s_row0 + r : t0 + r - kRowsA;
+        const bool in = p < np && sn >= 0 && sn < (is_les ? A.n_les : A.n_ff);
+        stage[r * LD + p] = in ? (is_les ? les : ff)[(size_t)sn * (size_t)A.npts + (size_t)(p0 + p)] : T(0);
+      }
     }
     __syncthreads();
-    if (valid) {
-      for (int p = 0; p < np; ++p) {
-        const T a = sa[ra][p], b = sb[i][p];
-        const T d = a - b;
-        d2.add_prod(d, d);
-        cr.add_prod(a - am, b - bm);
+    if (any) {
+      const int nv = np / W;
+      int q = 0;
+      for (; q + kFold <= nv; q += kFold) {
+#pragma unroll
+        for (int i = 0; i < kFold; ++i) pair_terms<T, W>(rows, (q + i) * W, c, cd, cc);
+        fold<T, W>(cd, cc, td, tc);
+      }
+      if (q < nv) {
+        for (; q < nv; ++q) pair_terms<T, W>(rows, q * W, c, cd, cc);
+        fold<T, W>(cd, cc, td, tc);
+      }
+      if (nv * W < np) {
+        T ed[4][1] = {}, ec[4][1] = {};
+        for (int p = nv * W; p < np; ++p) pair_terms<T, 1>(rows, p, c, ed, ec);
+        fold<T, 1>(ed, ec, td, tc);
       }
     }
   }
-  if (valid) {
-    double* o = A.part + 2 * (((size_t)blockIdx.x * A.n_ff + t) * A.nlag + jl);
-    o[0] = d2.value();
-    o[1] = cr.value();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!valid[k]) continue;
+    const int t = t0 + ti + kPairW * (k >> 1), jl = j0 + li + kPairW * (k & 1);
+    double* o = A.part + 2 * (((size_t)t * A.nlag + jl) * gridDim.x + blockIdx.x);
+    o[0] = td[k].value();
+    o[1] = tc[k].value();
   }
 }
 
@@ -205,64 +358,115 @@ struct FinishArgs {
   double* pcc;
 };
 
-__global__ void series_finish_kernel(FinishArgs A) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per pair: lane c sums chunks c, c + 32, ... and a fixed butterfly adds the lanes
+constexpr int kFinishThreads = 256;
+__global__ void __launch_bounds__(kFinishThreads) series_finish_kernel(FinishArgs A) {
+  const size_t idx = (size_t)blockIdx.x * (kFinishThreads / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (idx >= (size_t)A.n_ff * A.nlag) return;
   const int t = int(idx / A.nlag), j = int(idx - (size_t)t * A.nlag);
   const int s = t - (A.lag_min + j);
   if (s < 0 || s >= A.n_les) {
-    A.dist[idx] = NAN;
-    A.pcc[idx] = NAN;
+    if (lane == 0) {
+      A.dist[idx] = NAN;
+      A.pcc[idx] = NAN;
+    }
     return;
   }
   double d2 = 0.0, cr = 0.0;
-  for (int c = 0; c < A.nchunk; ++c) {
-    const double* o = A.part + 2 * ((size_t)c * A.n_ff * A.nlag + idx);
-    d2 += o[0];
-    cr += o[1];
+  const double* o = A.part + 2 * idx * (size_t)A.nchunk;
+  for (int c = lane; c < A.nchunk; c += 32) {
+    d2 += o[2 * c];
+    cr += o[2 * c + 1];
   }
+  for (int m = 16; m > 0; m >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, m);
+    cr += __shfl_xor_sync(0xffffffffu, cr, m);
+  }
+  if (lane != 0) return;
   // the pairs kernel centred on the means rounded to the working precision:
   // sum (a - a_c)(b - b_c) = sum (a - mean_a)(b - mean_b) + n (mean_a - a_c)(mean_b - b_c)
   const double ma = A.mom.mean[s], mb = A.mom.mean[A.n_les + t];
   const double ca = A.fp32 ? double(float(ma)) : ma, cb = A.fp32 ? double(float(mb)) : mb;
   cr -= double(A.npts) * (ma - ca) * (mb - cb);
   A.dist[idx] = d2;
-  const double va = snapshot_css(A.mom, s, A.fp32), vb = snapshot_css(A.mom, A.n_les + t, A.fp32);
-  A.pcc[idx] = (va > 0.0 && vb > 0.0) ? cr / (sqrt(va) * sqrt(vb)) : NAN;
+  const double ra = A.mom.rnorm[s], rb = A.mom.rnorm[A.n_les + t];
+  A.pcc[idx] = (ra > 0.0 && rb > 0.0) ? cr * ra * rb : NAN;
 }
 
-// mean distance per lag over the defined pairs, and its argmin (Eq. 16)
-__global__ void series_phase_kernel(const double* dist, int n_ff, int nlag, int lag_min, double* mean_dist,
-                                    int* phase) {
-  for (int j = threadIdx.x; j < nlag; j += blockDim.x) {
+// Does lag phi with mean distance m come before lag pb with mean mb?  Smaller
+// mean, then smaller |phi|, then the negative lag: a total order on the lags.
+__device__ __forceinline__ bool lag_before(double m, int phi, double mb, int pb) {
+  if (m != mb) return m < mb;
+  const int aphi = phi < 0 ? -phi : phi, apb = pb < 0 ? -pb : pb;
+  return aphi < apb || (aphi == apb && phi < pb);
+}
+
+// Mean distance per lag over the defined pairs (a warp per lag, lane-strided
+// over the snapshots, fixed butterfly), then, in the last CTA to finish, its
+// argmin (Eq. 16) by a block reduction; the order is total, so the argmin does
+// not depend on the reduction's order.  phase: [lag, found, CTAs done] (the
+// counter starts at zero).
+constexpr int kPhaseThreads = 256;
+__device__ __forceinline__ void argmin_step(int& best, double& mb, int ob, double om, int lag_min) {
+  if (ob >= 0 && (best < 0 || lag_before(om, lag_min + ob, mb, lag_min + best))) best = ob, mb = om;
+}
+
+__global__ void __launch_bounds__(kPhaseThreads) series_phase_kernel(const double* dist, int n_ff, int nlag,
+                                                                     int lag_min, double* mean_dist, int* phase) {
+  constexpr int kWarps = kPhaseThreads / 32;
+  __shared__ double wm[kWarps];
+  __shared__ int wj[kWarps];
+  __shared__ int is_last;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * kWarps + warp;
+  if (j < nlag) {
     double s = 0.0;
     int n = 0;
-    for (int t = 0; t < n_ff; ++t) {
+    for (int t = lane; t < n_ff; t += 32) {
       const double v = dist[(size_t)t * nlag + j];
       if (!isnan(v)) {
         s += v;
         ++n;
       }
     }
-    mean_dist[j] = n ? s / double(n) : NAN;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int best = -1;
-    for (int j = 0; j < nlag; ++j) {
-      const double m = mean_dist[j];
-      if (isnan(m)) continue;
-      if (best < 0) {
-        best = j;
-        continue;
-      }
-      const double mb = mean_dist[best];
-      const int phi = lag_min + j, pb = lag_min + best;
-      const int aphi = phi < 0 ? -phi : phi, apb = pb < 0 ? -pb : pb;
-      if (m < mb || (m == mb && (aphi < apb || (aphi == apb && phi < pb)))) best = j;
+    for (int m = 16; m > 0; m >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, m);
+      n += __shfl_xor_sync(0xffffffffu, n, m);
     }
-    phase[0] = best < 0 ? 0 : lag_min + best;
-    phase[1] = best >= 0;
+    if (lane == 0) mean_dist[j] = n ? s / double(n) : NAN;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&phase[2], 1) == int(gridDim.x) - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  int best = -1;
+  double mb = 0.0;
+  for (int k = threadIdx.x; k < nlag; k += kPhaseThreads) {
+    const double m = __ldcg(mean_dist + k);
+    if (!isnan(m)) argmin_step(best, mb, k, m, lag_min);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const double om = __shfl_xor_sync(0xffffffffu, mb, o);
+    argmin_step(best, mb, ob, om, lag_min);
+  }
+  if (lane == 0) wm[warp] = mb, wj[warp] = best;
+  __syncthreads();
+  if (warp == 0) {
+    best = lane < kWarps ? wj[lane] : -1;
+    mb = lane < kWarps ? wm[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const double om = __shfl_xor_sync(0xffffffffu, mb, o);
+      argmin_step(best, mb, ob, om, lag_min);
+    }
+    if (lane == 0) {
+      phase[0] = best < 0 ? 0 : lag_min + best;
+      phase[1] = best >= 0;
+    }
   }
 }
 
@@ -271,19 +475,53 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+// Device memory pool of the lag-table scratch, one per device, created on
+// first use: blocks a call frees go back to the pool (release threshold
+// unlimited), so a later call takes them again without a driver allocation and
+// without the device-wide synchronisation of cudaFree.
+cudaMemPool_t scratch_pool(int dev) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &pp) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return nullptr;
+    }
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+// One call's scratch, allocated and freed in the order of the call's stream.
 struct Scratch {
+  cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
   std::vector<void*> ptrs;
   cudaError_t err = cudaSuccess;
+  explicit Scratch(cudaStream_t s) : st(s) {
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess && !(pool = scratch_pool(dev))) err = cudaErrorMemoryAllocation;
+  }
   void* get(size_t bytes) {
     void* p = nullptr;
     if (err != cudaSuccess) return nullptr;
-    err = cudaMalloc(&p, bytes ? bytes : 16);
+    err = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, st);
     if (err != cudaSuccess) return nullptr;
     ptrs.push_back(p);
     return p;
   }
   ~Scratch() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, st);
   }
 };
 
@@ -319,28 +557,40 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // moments: a few waves of (chunk, snapshot) CTAs, at least 1024 points per CTA
+  // moments: (snapshot, slice) CTAs, slices of at most 64 KB (the slices resident at once fit in L2, so
+  // each CTA's second read of its slice hits it), at least four CTAs per SM, at least 1024 points a slice
   const int nsnap = n_les + n_ff;
-  int64_t mchunks = (4 * (int64_t)nsm + nsnap - 1) / nsnap;
+  const int64_t slice_pts = 65536 / (int64_t)sizeof(T);
+  int64_t mchunks = (npts + slice_pts - 1) / slice_pts;
+  const int64_t min_mchunks = (4 * (int64_t)nsm + nsnap - 1) / nsnap;
+  if (mchunks < min_mchunks) mchunks = min_mchunks;
   const int64_t max_mchunks = (npts + 1023) / 1024;
   if (mchunks > max_mchunks) mchunks = max_mchunks;
   if (mchunks > 65535) mchunks = 65535;
   if (mchunks < 1) mchunks = 1;
   const int64_t mchunk = (npts + mchunks - 1) / mchunks;
   mchunks = (npts + mchunk - 1) / mchunk;
-  double* mbuf = static_cast<double*>(S.get(sizeof(double) * ((size_t)2 * nsnap * mchunks + nsnap)));
+  double* mbuf = static_cast<double*>(S.get(sizeof(double) * ((size_t)2 * nsnap * mchunks + 2 * (size_t)nsnap)));
   if (!mbuf) return S.err;
-  MomArgs M{n_les, nsnap, (int)mchunks, npts, mchunk, mbuf, mbuf + (size_t)nsnap * mchunks,
-            mbuf + (size_t)2 * nsnap * mchunks};
+  double* mean = mbuf + (size_t)2 * nsnap * mchunks;
+  MomArgs M{n_les, nsnap, (int)mchunks, npts, mchunk, mbuf, mbuf + (size_t)nsnap * mchunks, mean, mean + nsnap};
   const double* mean_les = M.mean;
   const double* mean_ff = M.mean + n_les;
 
   // split the points into chunks: a few waves of CTAs over the SMs, partials within budget
   const int tiles_t = (n_ff + kTileT - 1) / kTileT, tiles_l = (nlag + kTileL - 1) / kTileL;
-  const int64_t P = Stage<T>::P;
+  // 16-byte staging when every staged row starts on a 16-byte boundary
+  const bool vec = npts % Vec<T>::W == 0 && reinterpret_cast<uintptr_t>(les) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(ff) % 16 == 0;
+  void (*const pairs)(const T*, const T*, PairArgs) =
+      vec ? series_pairs_kernel<T, true> : series_pairs_kernel<T, false>;
+  const int64_t P = kStageBytes / sizeof(T);
   const int64_t rounds = (npts + P - 1) / P;
   const int64_t tiles = (int64_t)tiles_t * tiles_l;
-  int64_t nchunk = (4 * (int64_t)nsm + tiles - 1) / tiles;
+  // about three waves of resident pair CTAs (tiles at the edges of the pair grid finish early)
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pairs, kPairThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+  int64_t nchunk = (3 * (int64_t)occ * nsm + tiles - 1) / tiles;
   const int64_t per_chunk_bytes = 16 * (int64_t)n_ff * nlag;
   const int64_t cap = (int64_t)kPartialBytes / per_chunk_bytes;
   if (nchunk > cap) nchunk = cap;
@@ -350,19 +600,25 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   nchunk = (npts + chunk - 1) / chunk;
   double* part = static_cast<double*>(S.get((size_t)per_chunk_bytes * nchunk));
   if (!part) return S.err;
+  cudaError_t e = cudaMemsetAsync(d_phase, 0, 3 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   tm.mark(0);
-  series_sum_kernel<T><<<dim3(nsnap, (unsigned)mchunks), kThreads, 0, st>>>(les, ff, M);
-  series_sq_kernel<T><<<dim3(nsnap, (unsigned)mchunks), kThreads, 0, st>>>(les, ff, M);
+  series_moments_kernel<T><<<dim3(nsnap, (unsigned)mchunks), kThreads, 0, st>>>(les, ff, M);
+  const int per_norm = kNormThreads / 32;
+  series_norm_kernel<<<(nsnap + per_norm - 1) / per_norm, kNormThreads, 0, st>>>(M, sizeof(T) == 4);
   tm.mark(1);
   PairArgs pa{n_les, n_ff, lag_min, nlag, npts, chunk, mean_les, mean_ff, part};
-  series_pairs_kernel<T><<<dim3((unsigned)nchunk, tiles_t, tiles_l), kThreads, 0, st>>>(les, ff, pa);
+  pairs<<<dim3((unsigned)nchunk, tiles_t, tiles_l), kPairThreads, 0, st>>>(les, ff, pa);
   tm.mark(2);
 
   FinishArgs fa{n_les, n_ff, lag_min, nlag, (int)nchunk, sizeof(T) == 4, npts, part, M, d_dist, d_pcc};
   const size_t npair = (size_t)n_ff * nlag;
-  series_finish_kernel<<<(unsigned)((npair + 255) / 256), 256, 0, st>>>(fa);
+  const size_t per_cta = kFinishThreads / 32;
+  series_finish_kernel<<<(unsigned)((npair + per_cta - 1) / per_cta), kFinishThreads, 0, st>>>(fa);
   tm.mark(3);
-  series_phase_kernel<<<1, 256, 0, st>>>(d_dist, n_ff, nlag, lag_min, d_mean, d_phase);
+  const int per_phase = kPhaseThreads / 32;
+  series_phase_kernel<<<(nlag + per_phase - 1) / per_phase, kPhaseThreads, 0, st>>>(d_dist, n_ff, nlag, lag_min,
+                                                                                    d_mean, d_phase);
   tm.mark(4);
   return cudaGetLastError();
 }
@@ -394,7 +650,7 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t esz = dtype == QG_FP32 ? 4 : 8;
-  Scratch S;
+  Scratch S(st);
   const void* dl = les;
   const void* df = ff;
   if (!on_device) {
@@ -413,7 +669,7 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
   }
   const size_t npair = (size_t)n_ff_snap * nlag;
   double* d_out = static_cast<double*>(S.get(sizeof(double) * (2 * npair + nlag)));
-  int* d_phase = static_cast<int*>(S.get(2 * sizeof(int)));
+  int* d_phase = static_cast<int*>(S.get(3 * sizeof(int)));  // phase, found, phase CTAs done
   if (!d_out || !d_phase) return fail(QG_ERR_OOM, "qg_series_compare: device allocation failed");
   Timer tm;
   tm.start(kernel_ms != nullptr, st);

@@ -115,6 +115,31 @@ def test_series_compare_device_matches_host_bitwise(dtype):
     assert host["phase"] == dev["phase"]
 
 
+@pytest.mark.parametrize("dtype,dist_tol,pcc_tol", [("float32", 1e-6, 1e-6), ("float64", 1e-12, 1e-12)])
+def test_series_compare_unaligned_device_series(dtype, dist_tol, pcc_tol):
+    """Series that start off a 16-byte boundary are staged element by element instead of by bulk copies
+    (other round lengths, so other point chunks): the same table up to summation order."""
+    import torch
+    les, ff = series_pair(21, 18, (32, 48), -2)
+    les, ff = les.astype(dtype), ff.astype(dtype)
+    aligned = qg.qg_series_compare(torch.from_numpy(les).cuda(), torch.from_numpy(ff).cuda(), -7, 5)
+    tdt = getattr(torch, dtype)
+    bl = torch.zeros(les.size + 1, dtype=tdt, device="cuda")
+    bf = torch.zeros(ff.size + 1, dtype=tdt, device="cuda")
+    dl = bl[1:].view(les.shape)
+    df = bf[1:].view(ff.shape)
+    dl.copy_(torch.from_numpy(les))
+    df.copy_(torch.from_numpy(ff))
+    assert dl.data_ptr() % 16 != 0
+    torch.cuda.synchronize()
+    off = qg.qg_series_compare(dl, df, -7, 5)
+    ref_d, ref_p = O.lag_table(les.astype(np.float64), ff.astype(np.float64), -7, 5)
+    check_table(aligned, ref_d, ref_p, -7, dist_tol, pcc_tol)
+    check_table(off, ref_d, ref_p, -7, dist_tol, pcc_tol)
+    ok = ~np.isnan(ref_d)
+    assert np.allclose(off["dist"][ok], aligned["dist"][ok], rtol=dist_tol, atol=0)
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_phase_of_a_translating_pattern(dtype):
     for shift in (-4, 0, 3):
@@ -143,6 +168,29 @@ def test_series_compare_edge_cases():
         qg.qg_series_compare(np.zeros((2, 4)), np.zeros((2, 4)), 1, -1)
     with pytest.raises(ValueError):
         qg.qg_series_compare(np.zeros((2, 4)), np.zeros((2, 5)), 0, 0)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_phase_tie_rules(dtype):
+    """Integer-valued series: every distance and mean is exact, so ties at the minimum are real ties
+    and the argmin must follow the rule (smallest |phi|, then the negative lag)."""
+    rng = np.random.default_rng(0)
+    kinds = set()
+    for _ in range(400):
+        n = int(rng.integers(3, 7))
+        npts = int(rng.integers(1, 4))
+        les = rng.integers(0, 4, (n, npts)).astype(dtype)
+        ff = rng.integers(0, 4, (n, npts)).astype(dtype)
+        ref_d, ref_p = O.lag_table(les.astype(np.float64), ff.astype(np.float64), -2, 2)
+        phi, mean = O.phase_shift(ref_d, -2)
+        got = qg.qg_series_compare(les, ff, -2, 2)
+        assert np.array_equal(got["dist"], ref_d, equal_nan=True)
+        assert np.array_equal(got["mean_dist"], mean, equal_nan=True)
+        assert got["phase"] == phi
+        tied = [j - 2 for j in range(5) if mean[j] == np.nanmin(mean)]
+        if len(tied) > 1:
+            kinds.add("sign" if 0 not in tied and -phi in tied else "abs")
+    assert kinds == {"abs", "sign"}  # both tie rules were exercised
 
 
 def test_series_compare_full_size_sampled():
