@@ -112,6 +112,31 @@ def algorithmic_bytes(wl, precision_fp32: bool):
     return out
 
 
+# Full-field round-trip model of one RK3 step: every 2-D transform moves one
+# N x N field (U_N = N^2 b bytes) out of its first pass and into its second;
+# stage I/O adds the reads of w_s (and w_0) and the write of w_{s+1}, and the
+# dynamic closures write and read J and D.  U_N traversals per RK stage by
+# closure; the Brinkman sub-step adds 11 and the sponge sub-step 7 (their
+# factor-field reads included).
+FIELD_TRAVERSALS_PER_STAGE = {S.NONE: 14, S.SMAG: 22, S.LEITH: 18, S.DSMAG: 43, S.DLEITH: 35}
+
+
+def field_model_bytes(wl, precision_fp32: bool):
+    """(row-pass bytes per launch, RK3 step bytes) in the full-field round-trip model.
+
+    A stage's row pass takes the row halves of its transforms: it reads the nin
+    inverse-transform intermediates and writes the nout forward ones, one U_N
+    each.
+    """
+    un = wl.n * wl.n * (4 if precision_fp32 else 8)
+    nin = {S.NONE: 4, S.LEITH: 4, S.SMAG: 6, S.DLEITH: 8, S.DSMAG: 12}[wl.closure]
+    nout = {S.NONE: 1, S.LEITH: 3, S.SMAG: 3, S.DLEITH: 6, S.DSMAG: 6}[wl.closure]
+    step = 3 * FIELD_TRAVERSALS_PER_STAGE[wl.closure]
+    step += 11 if wl.geometry != "none" else 0
+    step += 7 if wl.sponge else 0
+    return (nin + nout) * un, step * un
+
+
 def algorithmic_bytes_ab2cn(wl, precision_fp32: bool):
     """Minimal HBM bytes per launch of each kernel class of one AB2CN step (Eq. 4), steady state.
 
@@ -753,8 +778,9 @@ def m_launches(m) -> int:
 # ---------------------------------------------------------------------------
 ADJ = {"n": 256, "n_fr": 1024, "steps": 400, "obs_first": 100, "obs_every": 20, "checkpoint": 20, "c": 0.17,
        "seed": 5, "beta": 5.0, "U": 0.5, "radius": 0.4}
-ADJ_METRIC = ("grid-pt-steps/s of the loss gradient (forward + checkpointed adjoint), 256^2 Smagorinsky FP64 LES, "
-              "400 steps, MSE against a filtered 1024^2 run")
+def adj_metric(precision: str = "fp64") -> str:
+    return (f"grid-pt-steps/s of the loss gradient (forward + checkpointed adjoint), 256^2 Smagorinsky "
+            f"{precision.upper()} LES, 400 steps, MSE against a filtered 1024^2 run")
 
 
 def adjoint_workload():
@@ -811,7 +837,8 @@ def run_adjoint_reference(args, budget):
     done, el = time_adjoint_oracle(les, budget)
     value = les.n * les.n * done / el
     line = {
-        "metric": ADJ_METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": done,
+        "metric": adj_metric(args.precision), "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1,
+        "steps": done,
         "warmup": 0, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": "adjoint256", **ADJ},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -842,9 +869,12 @@ def run_adjoint_bench(args):
     stream = torch.cuda.Stream()
     w0_les, targets = adjoint_targets(qg, fr, obs, stream)
     n, K, ce = les.n, ADJ["steps"], ADJ["checkpoint"]
-    solver = qg.QGSolver.from_workload(les, precision=qg.QG_FP64, stream=stream)
-    tgt = {k: torch.from_numpy(t).cuda() for k, t in zip(obs, targets)}
-    w0 = torch.from_numpy(w0_les).cuda()
+    fp32 = args.precision == "fp32"
+    tdt = torch.float32 if fp32 else torch.float64
+    ndt = np.float32 if fp32 else np.float64
+    solver = qg.QGSolver.from_workload(les, precision=qg.QG_FP32 if fp32 else qg.QG_FP64, stream=stream)
+    tgt = {k: torch.from_numpy(t.astype(ndt)).cuda() for k, t in zip(obs, targets)}
+    w0 = torch.from_numpy(w0_les.astype(ndt)).cuda()
     scale = 2.0 / (len(obs) * n * n)
 
     need = sorted(set(range(0, K, ce)) | set(obs))
@@ -857,7 +887,7 @@ def run_adjoint_bench(args):
         for t in need:
             solver.step(t - k)
             k = t
-            st_ = solver.get_state(out=torch.empty((n, n), dtype=torch.float64, device="cuda"))
+            st_ = solver.get_state(out=torch.empty((n, n), dtype=tdt, device="cuda"))
             if t % ce == 0 and t < K:
                 ckpts[t] = st_
             if t in tgt:
@@ -914,8 +944,8 @@ def run_adjoint_bench(args):
     e1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / K
-    st = solver.get_state(out=torch.empty((n, n), dtype=torch.float64, device="cuda"))
-    lam1 = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    st = solver.get_state(out=torch.empty((n, n), dtype=tdt, device="cuda"))
+    lam1 = torch.randn((n, n), dtype=tdt, device="cuda")
     for _ in range(3):
         solver.step_vjp(st, lam1)
     torch.cuda.synchronize()
@@ -937,8 +967,9 @@ def run_adjoint_bench(args):
     lib.qg_profile(solver.h, 0)
     cls = {KERNEL_CLASSES[i]: (int(counts[i]), float(kms[i])) for i in range(nk) if counts[i]}
     Kb = (n - 1) // 3
-    I = n * (Kb + 1) * 16
-    R = n * n * 8
+    esz = 4 if fp32 else 8
+    I = n * (Kb + 1) * 2 * esz
+    R = n * n * esz
     n_row, t_row = cls.get("adj_row", (0, 0.0))
     achieved = (R + I) * n_row / (t_row / 1e3) / 1e9 if t_row else 0.0
     peaks, peak_src = measured_peaks()
@@ -949,14 +980,15 @@ def run_adjoint_bench(args):
                 "avg_launch_us": 1e3 * t_row / n_row if n_row else None,
                 "class_ms_per_vjp": {k: v[1] / 5 for k, v in cls.items()},
                 "class_launches_per_vjp": {k: v[0] / 5 for k, v in cls.items()},
-                "note": "256^2 FP64 fields (0.5 MB) stay in the 126 MB L2: these launches are latency-bound",
+                "note": f"256^2 {args.precision.upper()} fields ({R / 2**20:.2f} MB) stay in the 126 MB L2: "
+                        "these launches are latency-bound",
                 "measured_in": "CUDA events around each launch of 5 eager adjoint steps"}
 
     # end to end: host initial field and targets in, gradient out
     barrier()
     t0 = time.perf_counter()
-    w_host = w0_les.copy()
-    tg_host = {k: t.copy() for k, t in zip(obs, targets)}
+    w_host = w0_les.astype(ndt)
+    tg_host = {k: t.astype(ndt) for k, t in zip(obs, targets)}
     tgt = {k: torch.from_numpy(t).cuda() for k, t in tg_host.items()}
     ck, states = forward(torch.from_numpy(w_host).cuda())
     g_obs = {t: scale * (states[t] - tgt[t]) for t in obs}
@@ -971,8 +1003,9 @@ def run_adjoint_bench(args):
                    "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward steps + 1 "
                              f"full_step_vjp each) of the 256^2 LES, {el:.1f} s"}
         line = {
-            "metric": ADJ_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": reps, "warmup": args.warmup,
-            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": adj_metric(args.precision), "value": value, "unit": UNIT, "n_gpus": world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
             "data": "synthetic",
             "config": {"workload": "adjoint256", **ADJ, "observed_steps": len(obs), "loss": loss,
                        "grad_norm": float(lam.norm().item()), "dloss_dc": g["c"], "dloss_drate": g["sponge_rate"],
@@ -1007,7 +1040,8 @@ def main():
     ap.add_argument("--workload", default="island2048-dleith", choices=sorted(WORKLOADS) + sorted(TOOLS))
     ap.add_argument("--scheme", default="rk3", choices=sorted(SCHEMES),
                     help="time scheme: rk3 (SSP-RK3 with exact sub-steps) or ab2cn (the paper's Eq. 4)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
+                    help="working precision (default: fp64 for the adjoint workload, fp32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 throughput / error leg")
@@ -1016,6 +1050,8 @@ def main():
     ap.add_argument("--no-torch-context", action="store_true",
                     help="skip timing the torch.fft (cuFFT) form of the step beside libqg")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "adjoint256" else "fp32"
     if args.warmup < 3 and args.impl != "reference":
         raise SystemExit("--warmup must be >= 3")
     if args.workload in TOOLS:
@@ -1125,12 +1161,25 @@ def main():
                 rec[k.strip()] = v.strip()
         if rec.get("traffic_kernel_class") == dom and rec.get("traffic_bytes_per_launch"):
             traffic = int(rec["traffic_bytes_per_launch"])
+    step_s = ms / 1e3 / args.steps
+    band = {"bytes_per_launch": bytes_launch, "achieved": achieved, "frac": achieved / peak,
+            "step_bytes": step_bytes, "step_frac": step_bytes / step_s / 1e9 / peak,
+            "model": "band storage: the arrays this design keeps (N x (K+1) mixed, (K+1) x (2K+1) spectral, "
+                     "N x N physical), each read or written once"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "peak_source": peak_src,
                 "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
-                "step_model_bytes": step_bytes,
-                "step_frac": step_bytes / (ms / 1e3 / args.steps) / 1e9 / peak,
                 "measured_in": "CUDA events around each launch, second pass of the same K steps"}
+    if dom == "row_stage":
+        # the full-field round-trip model: the reported achieved / frac; the band model beside it
+        row_b, step_fb = field_model_bytes(wl, fp32)
+        roofline.update({"achieved": row_b / avg_s / 1e9, "frac": row_b / avg_s / 1e9 / peak,
+                         "bytes_per_launch": row_b,
+                         "model": "full-field round trips: each 2-D transform moves one N^2 field between "
+                                  "its passes; the row pass reads nin and writes nout such fields"})
+        if scheme == 0:
+            roofline.update({"step_model_bytes": step_fb, "step_frac": step_fb / step_s / 1e9 / peak})
+    roofline["band_model"] = band
 
     # ---- end to end through the public API with host buffers
     torch.cuda.synchronize()

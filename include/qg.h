@@ -124,14 +124,24 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
               const qg_closure* closure, const qg_params* params, void* cuda_stream, qg_handle** out);
 
 /* Set the state from a physical vorticity field of N*N values (dtype QG_FP64
- * = double, QG_FP32 = float; host if on_device = 0, device otherwise).  The
- * field is projected: w_hat = T F[w] with the mean mode removed (Sec. II-C,
- * II-D).  Resets the non-finite flag; keeps t and step. */
+ * = double, QG_FP32 = float; host if on_device = 0, device otherwise: read on
+ * the handle's stream, see qg_stream).  The field is projected: w_hat =
+ * T F[w] with the mean mode removed (Sec. II-C, II-D).  Resets the non-finite
+ * flag; keeps t and step. */
 int qg_set_state(qg_handle* h, const void* omega, int32_t on_device, int32_t dtype);
 
 /* Write the physical vorticity of the current state (N*N, dtype as above).
- * Synchronises the handle's stream when omega is a host buffer. */
+ * Synchronises the handle's stream when omega is a host buffer; a device
+ * buffer is written on the handle's stream (see qg_stream). */
 int qg_get_state(qg_handle* h, void* omega, int32_t on_device, int32_t dtype);
+
+/* The cudaStream_t (as void*) the handle enqueues its work on: the stream
+ * given at create, or the handle's own stream for an ensemble member (NULL is
+ * the legacy default stream).  Device buffers passed to qg_set_state,
+ * qg_get_state and qg_step_vjp are read and written in the order of this
+ * stream: the caller makes it wait for the producer of an input and makes the
+ * consumer of an output wait for it.  No paper counterpart (plumbing). */
+int qg_stream(qg_handle* h, void** stream);
 
 /* Enqueue nsteps >= 0 steps (asynchronous).  Returns QG_ERR_NONFINITE without
  * enqueueing if an earlier step is already known to have produced a

@@ -65,6 +65,7 @@ SIGNATURES = {
     "qg_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "qg_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_sync": (C.c_int, [C.c_void_p]),
+    "qg_stream": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "qg_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(qg_diag)]),
     "qg_destroy": (None, [C.c_void_p]),
     "qg_sgs_apriori": (C.c_int, [DP, C.c_int32, C.c_int32, C.c_double, DP, DP, C.POINTER(qg_closure),

@@ -1583,6 +1583,12 @@ void qg_destroy(qg_handle* h) {
   delete h;
 }
 
+int qg_stream(qg_handle* h, void** stream) {
+  if (!h || !stream) return fail(QG_ERR_ARG, "qg_stream: NULL argument");
+  *stream = static_cast<void*>(h->stream);
+  return QG_OK;
+}
+
 int qg_set_state(qg_handle* h, const void* omega, int32_t on_device, int32_t dtype) {
   if (!h || !omega) return fail(QG_ERR_ARG, "qg_set_state: NULL argument");
   if (dtype != QG_FP32 && dtype != QG_FP64) return fail(QG_ERR_ARG, "qg_set_state: bad dtype");

@@ -2,7 +2,9 @@
 
 Host arrays are numpy float64/float32; device arrays are torch CUDA tensors
 (passed by data pointer, borrowed for the call).  Streams are torch streams
-or raw cudaStream_t integers.
+or raw cudaStream_t integers.  The functional calls leave the ordering of a
+handle's stream against other streams to the caller; QGSolver's methods and
+qg_series_compare order it against torch's current stream themselves.
 """
 from __future__ import annotations
 
@@ -15,7 +17,8 @@ import numpy as np
 from ._lib import (QG_ERR_NONFINITE, QG_FP32, QG_FP64, QG_OK, QGError, check, load, qg_closure, qg_diag, qg_grid,
                    qg_member, qg_params)
 
-__all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_step", "qg_sync", "qg_diagnostics", "qg_destroy",
+__all__ = ["qg_create", "qg_set_state", "qg_get_state", "qg_stream", "qg_step", "qg_sync", "qg_diagnostics",
+           "qg_destroy",
            "qg_sgs_apriori", "qg_grid_filter", "qg_series_compare", "qg_step_vjp", "qg_last_error", "qg_version",
            "QGSolver",
            "QGEnsemble"]
@@ -96,6 +99,45 @@ def qg_get_state(h: int, n: int, out=None, dtype=np.float64):
     ptr, dev, dt, keep = _buffer(out, n)
     check(load().qg_get_state(h, ptr, dev, dt), "qg_get_state")
     return out
+
+
+def qg_stream(h: int) -> int:
+    """The cudaStream_t (as an int, 0 = legacy default stream) the handle enqueues its work on."""
+    out = C.c_void_p(0)
+    check(load().qg_stream(h, C.byref(out)), "qg_stream")
+    return int(out.value or 0)
+
+
+class _Ordered:
+    """Orders a handle's stream against torch's current stream around a call with device tensors.
+
+    On entry the handle's stream waits for the current stream (whatever torch
+    queued that writes the inputs); on exit the current stream waits for the
+    handle's stream (so torch's later reads of the outputs, and the caching
+    allocator's reuse of their memory, come after the library's writes).
+    """
+
+    def __init__(self, h: int, active: bool):
+        self.h, self.active = h, active
+
+    def __enter__(self):
+        if self.active:
+            import torch
+            self.cur = torch.cuda.current_stream()
+            ptr = qg_stream(self.h)
+            self.hs = self.cur if ptr == self.cur.cuda_stream else (
+                torch.cuda.default_stream() if ptr == 0 else torch.cuda.ExternalStream(ptr))
+            if self.hs is not self.cur:
+                self.hs.wait_stream(self.cur)
+        return self
+
+    def __exit__(self, *exc):
+        if self.active and self.hs is not self.cur:
+            self.cur.wait_stream(self.hs)
+
+
+def _on_device(*xs) -> bool:
+    return any(hasattr(x, "is_cuda") and x.is_cuda for x in xs if x is not None)
 
 
 def qg_step(h: int, nsteps: int = 1) -> None:
@@ -216,6 +258,14 @@ def qg_series_compare(les, ff, lag_min: int, lag_max: int, stream=None, timing: 
     phase = C.c_int32(0)
     kms = np.zeros(4)
     P = C.POINTER(C.c_double)
+    if dev_a:
+        # the call's stream waits for torch's current stream (the series' producer); the call
+        # synchronises its stream before it returns
+        import torch
+        cur = torch.cuda.current_stream()
+        sp = _stream_ptr(stream) or 0
+        if sp != cur.cuda_stream:
+            (torch.cuda.default_stream() if sp == 0 else torch.cuda.ExternalStream(sp)).wait_stream(cur)
     rc = load().qg_series_compare(pa, na, pb, nb, npa, da, dev_a, int(lag_min), int(lag_max), _stream_ptr(stream),
                                   dist.ctypes.data_as(P), pcc.ctypes.data_as(P), mean.ctypes.data_as(P),
                                   C.byref(phase), kms.ctypes.data_as(P) if timing else None)
@@ -252,11 +302,15 @@ class QGSolver:
                    sponge=wl.sponge_field(), kind=wl.closure, c=wl.c, test_ratio=wl.test_ratio, dt=wl.dt,
                    nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, scheme=scheme, stream=stream)
 
+    # Device tensors are ordered against torch's current stream (see _Ordered),
+    # so callers may mix these calls with torch ops on any stream.
     def set_state(self, omega) -> None:
-        qg_set_state(self.h, omega, self.cfg.n)
+        with _Ordered(self.h, _on_device(omega)):
+            qg_set_state(self.h, omega, self.cfg.n)
 
     def get_state(self, out=None, dtype=np.float64):
-        return qg_get_state(self.h, self.cfg.n, out, dtype)
+        with _Ordered(self.h, _on_device(out)):
+            return qg_get_state(self.h, self.cfg.n, out, dtype)
 
     def step(self, nsteps: int = 1) -> None:
         qg_step(self.h, nsteps)
@@ -265,7 +319,8 @@ class QGSolver:
         qg_sync(self.h)
 
     def step_vjp(self, omega_n, lam_next, lam_n=None):
-        return qg_step_vjp(self.h, self.cfg.n, omega_n, lam_next, lam_n)
+        with _Ordered(self.h, _on_device(omega_n, lam_next, lam_n)):
+            return qg_step_vjp(self.h, self.cfg.n, omega_n, lam_next, lam_n)
 
     def diagnostics(self, raise_nonfinite: bool = True) -> dict:
         return qg_diagnostics(self.h, raise_nonfinite)

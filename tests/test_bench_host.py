@@ -59,6 +59,26 @@ def test_algorithmic_byte_model_production():
     assert 1.2e9 < step < 1.3e9
 
 
+def test_full_field_model_counts_per_closure():
+    """Full-field round-trip model: 2 U_N per 2-D transform plus stage I/O; per step, with island and sponge:
+    none 60, Smagorinsky 84, Leith 72, dynamic Smagorinsky 147, dynamic Leith 123 U_N."""
+    import dataclasses
+    base = S.island2048_dleith()
+    un = base.n * base.n * 4
+    expect = {S.NONE: (5, 60), S.SMAG: (9, 84), S.LEITH: (7, 72), S.DSMAG: (18, 147), S.DLEITH: (14, 123)}
+    for kind, (row, step) in expect.items():
+        wl = dataclasses.replace(base, closure=kind)
+        assert bench.field_model_bytes(wl, True) == (row * un, step * un)
+    # each stage: the transforms' round trips (2 U_N each) plus 4 (static) or 7 (dynamic) U_N of stage I/O
+    ninv = {S.NONE: 4, S.SMAG: 6, S.LEITH: 4, S.DSMAG: 12, S.DLEITH: 8}
+    nfwd = {S.NONE: 1, S.SMAG: 3, S.LEITH: 3, S.DSMAG: 6, S.DLEITH: 6}
+    for kind, per_stage in bench.FIELD_TRAVERSALS_PER_STAGE.items():
+        io = 7 if kind in (S.DSMAG, S.DLEITH) else 4
+        assert per_stage == 2 * (ninv[kind] + nfwd[kind]) + io
+    row, step = bench.field_model_bytes(base, True)
+    assert abs(step - 2.064e9) < 1e6 and abs(row - 234.9e6) < 1e5
+
+
 def test_ab2cn_byte_model_at_2048_dynamic_leith():
     """One explicit evaluation per step: 38 mixed arrays, 13 spectra and the two factor fields (Eq. 4)."""
     wl = S.island2048_dleith()
