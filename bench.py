@@ -547,8 +547,14 @@ def run_series_bench(args):
     sm_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = nsm * 128 * sm_mhz * 1e6 / 1e12  # FP32-pipe instructions, Tinst/s
     achieved = pp * SERIES_INST / (avg["pairs"] / 1e3) / 1e12
+    traffic = None  # ncu DRAM bytes of one pairs launch, recorded beside the launch list
+    prof = os.path.join(ROOT, "profiles", "launches_series512_fp32.md")
+    if os.path.exists(prof):
+        rec = dict(line.split(":", 1) for line in open(prof) if line.startswith("traffic_") and ":" in line)
+        if rec.get("traffic_kernel", "").strip() == "series_pairs_kernel":
+            traffic = int(rec["traffic_bytes_per_launch"].strip())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s (FP32 pipe)",
-                "frac": achieved / peak, "traffic": None, "kernel": "series_pairs_kernel",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "series_pairs_kernel",
                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                 "inst_per_pair_point": SERIES_INST, "avg_launch_us": avg["pairs"] * 1e3,
                 "kernel_ms": avg,

@@ -41,7 +41,7 @@ constexpr int kTileT = 16;                   // ff snapshots per tile
 constexpr int kTileL = 16;                   // lags per tile
 constexpr int kRowsA = kTileT + kTileL - 1;  // les rows a tile touches
 constexpr int kThreads = kTileT * kTileL;
-constexpr int kMaxSnap = 1000000;  // keeps the pair grid's y extent (snapshots / 16) within 65535
+constexpr int kMaxSnap = 1000000;  // keeps the pair grid (tiles x chunks) within the launch limits
 constexpr int kMaxLag = 1 << 16;
 constexpr size_t kMaxPairs = size_t(1) << 24;
 constexpr size_t kPartialBytes = size_t(256) << 20;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kNormThreads) series_norm_kernel(MomArgs A, in
 }
 
 struct PairArgs {
-  int n_les, n_ff, lag_min, nlag;
+  int n_les, n_ff, lag_min, nlag, tiles_l;
   int64_t npts, chunk;
   const double* mean_les;
   const double* mean_ff;
@@ -265,8 +265,10 @@ __global__ void __launch_bounds__(kPairThreads) series_pairs_kernel(const T* __r
   constexpr int LD = P + W;                         // padded row length in elements
   constexpr int NQ = P / W;                         // vectors per staged row
   __shared__ __align__(16) T stage[kRowsStaged * LD];
+  // grid: x = pair tile (lags fastest), y = point chunk, so the tiles that share a chunk's rows run together
   const int ti = threadIdx.x / kPairW, li = threadIdx.x % kPairW;
-  const int t0 = blockIdx.y * kTileT, j0 = blockIdx.z * kTileL;
+  const int by = int(blockIdx.x) / A.tiles_l, bz = int(blockIdx.x) - by * A.tiles_l;
+  const int t0 = by * kTileT, j0 = bz * kTileL;
   const int s_row0 = t0 - A.lag_min - j0 - (kTileL - 1);  // les snapshot of staged row 0
   const int ra = ti - li + kTileL - 1;                     // les row of pairs (t, j) and (t + 8, j + 8)
   bool valid[4];
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kPairThreads) series_pairs_kernel(const T* __r
                             stage + (kRowsA + ti) * LD, stage + (kRowsA + ti + kPairW) * LD};
   SumAcc<T> td[4], tc[4];
   T cd[4][W] = {}, cc[4][W] = {};
-  const int64_t p_begin = (int64_t)blockIdx.x * A.chunk;
+  const int64_t p_begin = (int64_t)blockIdx.y * A.chunk;
   const int64_t p_end = p_begin + A.chunk < A.npts ? p_begin + A.chunk : A.npts;
   for (int64_t p0 = p_begin; p0 < p_end; p0 += P) {
     const int np = p_end - p0 < P ? int(p_end - p0) : P;
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kPairThreads) series_pairs_kernel(const T* __r
   for (int k = 0; k < 4; ++k) {
     if (!valid[k]) continue;
     const int t = t0 + ti + kPairW * (k >> 1), jl = j0 + li + kPairW * (k & 1);
-    double* o = A.part + 2 * (((size_t)t * A.nlag + jl) * gridDim.x + blockIdx.x);
+    double* o = A.part + 2 * (((size_t)t * A.nlag + jl) * gridDim.y + blockIdx.y);
     o[0] = td[k].value();
     o[1] = tc[k].value();
   }
@@ -595,6 +597,7 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   const int64_t cap = (int64_t)kPartialBytes / per_chunk_bytes;
   if (nchunk > cap) nchunk = cap;
   if (nchunk > rounds) nchunk = rounds;
+  if (nchunk > 65535) nchunk = 65535;
   if (nchunk < 1) nchunk = 1;
   const int64_t chunk = ((rounds + nchunk - 1) / nchunk) * P;
   nchunk = (npts + chunk - 1) / chunk;
@@ -607,8 +610,8 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   const int per_norm = kNormThreads / 32;
   series_norm_kernel<<<(nsnap + per_norm - 1) / per_norm, kNormThreads, 0, st>>>(M, sizeof(T) == 4);
   tm.mark(1);
-  PairArgs pa{n_les, n_ff, lag_min, nlag, npts, chunk, mean_les, mean_ff, part};
-  pairs<<<dim3((unsigned)nchunk, tiles_t, tiles_l), kPairThreads, 0, st>>>(les, ff, pa);
+  PairArgs pa{n_les, n_ff, lag_min, nlag, tiles_l, npts, chunk, mean_les, mean_ff, part};
+  pairs<<<dim3((unsigned)tiles, (unsigned)nchunk), kPairThreads, 0, st>>>(les, ff, pa);
   tm.mark(2);
 
   FinishArgs fa{n_les, n_ff, lag_min, nlag, (int)nchunk, sizeof(T) == 4, npts, part, M, d_dist, d_pcc};
