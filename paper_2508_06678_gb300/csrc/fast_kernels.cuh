@@ -15,7 +15,10 @@
 #define QG_COL_MINB 2
 #endif
 #ifndef QG_COL_MINB_REDUCE
-#define QG_COL_MINB_REDUCE 2
+#define QG_COL_MINB_REDUCE 3
+#endif
+#ifndef QG_LEAN_BATCH
+#define QG_LEAN_BATCH 4
 #endif
 #ifndef QG_COL_MINB_FWD
 #define QG_COL_MINB_FWD 1
@@ -54,6 +57,11 @@ template <int N> struct ColCfg {
   static constexpr int BR = fast_box_rows(N);  // rows per TMA box
   static constexpr int NBOX = N / BR;
 };
+// The FP32 Germano reduction keeps its cross-field sums in global scratch rather than registers and
+// stages its tiles through one buffer, so three CTAs fit on an SM and all K + 1 columns run in one wave.
+template <typename T, int OP> __host__ __device__ constexpr bool col_lean() {
+  return OP == CO_DYN_REDUCE && sizeof(T) == 4;
+}
 // bytes of one shared-memory stage: a dense W x N tile for TMA, or W padded exchange columns
 template <typename T, int N> __host__ __device__ constexpr int col_stage_bytes() {
   constexpr int dense = N * ColCfg<N>::W * 2 * (int)sizeof(T);
@@ -340,8 +348,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   __shared__ __align__(8) uint64_t mbar[2];
   // TMA tiles need 128-byte aligned shared addresses: align the base explicitly (1 KB slack is allocated)
   unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr bool LEAN = col_lean<T, OP>();
+  constexpr int NSTG = LEAN ? 1 : 2;  // TMA stages of the forward fields
   C* xbuf = reinterpret_cast<C*>(sbase);
-  C* stage[2] = {reinterpret_cast<C*>(sbase + SB), reinterpret_cast<C*>(sbase + 2 * SB)};
+  C* stage[2] = {reinterpret_cast<C*>(sbase + SB), reinterpret_cast<C*>(sbase + (NSTG == 2 ? 2 : 1) * SB)};
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
   const int mx = blockIdx.x * W + c;
@@ -353,13 +363,13 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   if (d.flag) {
     if (__syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0)) return;
   }
-  // thread 0 starts the first two forward fields' tiles
+  // thread 0 starts the first NSTG forward fields' tiles
   if (lead) {
     tma::mbar_init(&mbar[0], 1);
     tma::mbar_init(&mbar[1], 1);
     tma::fence_mbar_init();
     if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE && OP != CO_AB2CN_COMBINE) {
-      for (int f = 0; f < d.nfwd && f < 2; ++f) {
+      for (int f = 0; f < d.nfwd && f < NSTG; ++f) {
         tma::mbar_expect_tx(&mbar[f], FIELD_BYTES);
         for (int bx = 0; bx < NBOX; ++bx)
           tma::load_2d(reinterpret_cast<unsigned char*>(stage[f]) + (size_t)bx * BR * W * sizeof(C), &tm.in[f],
@@ -384,14 +394,15 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE && OP != CO_AB2CN_COMBINE) {
 #pragma unroll 1
     for (int f = 0; f < d.nfwd; ++f) {
-      const int sidx = f & 1;
+      const int sidx = f % NSTG;
+      const uint32_t par = (f / NSTG) & 1;
       C* st = stage[sidx];
-      const bool ok = tma::mbar_wait(&mbar[sidx], (f >> 1) & 1, kWaitCycles);
+      const bool ok = tma::mbar_wait(&mbar[sidx], par, kWaitCycles);
       if (__syncthreads_or(!ok)) {
         // a tile never arrived: report, give the copy one more bounded wait, leave together
         if (lead) {
           if (d.err) atomicOr(d.err, kFlagTimeout);
-          tma::mbar_wait(&mbar[sidx], (f >> 1) & 1, kWaitCycles);
+          tma::mbar_wait(&mbar[sidx], par, kWaitCycles);
         }
         __syncthreads();
         return;
@@ -400,17 +411,81 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
       for (int m = 0; m < E::EL; ++m) x[m] = st[(t + TT * m) * W + c];
       ph = 0;
       E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, -1);
-      // every thread is done with this stage: hand it to the TMA for field f + 2
+      // every thread is done with this stage: hand it to the TMA for field f + NSTG
       tma::fence_proxy_async();
       __syncthreads();
-      if (lead && f + 2 < d.nfwd) {
+      if (lead && f + NSTG < d.nfwd) {
         tma::mbar_expect_tx(&mbar[sidx], FIELD_BYTES);
         for (int bx = 0; bx < NBOX; ++bx)
-          tma::load_2d(reinterpret_cast<unsigned char*>(st) + (size_t)bx * BR * W * sizeof(C), &tm.in[f + 2],
+          tma::load_2d(reinterpret_cast<unsigned char*>(st) + (size_t)bx * BR * W * sizeof(C), &tm.in[f + NSTG],
                        2 * c0, bx * BR, &mbar[sidx]);
       }
+      if constexpr (LEAN) {
+        // The Germano reduction with its cross-field values in scratch (s0 = P, then the Brinkman
+        // partial; s1 = -D, then r^p P~ - D; s2 = H): the same operations as the register form below.
+        // Each thread reads back only what it wrote; a batch's loads are issued before its stores, since
+        // the arrays may alias as far as the compiler can tell.
+        C* s0 = reinterpret_cast<C*>(d.scr[0]);
+        C* s1 = reinterpret_cast<C*>(d.scr[1]);
+        C* s2 = reinterpret_cast<C*>(d.scr[2]);
+        constexpr int LB = QG_LEAN_BATCH;
+        static_assert(E::EL % LB == 0, "the load batch must divide the thread's elements");
 #pragma unroll
-      for (int m = 0; m < E::EL; ++m) {
+        for (int m0 = 0; m0 < E::EL; m0 += LB) {
+          C la[LB], lb[LB];
+#pragma unroll
+          for (int q = 0; q < LB; ++q) {
+            const int k = t + TT * (m0 + q);
+            const size_t gi = colbase + (k <= K ? k : k - N + Ny);
+            la[q] = mk<C>(T(0), T(0));
+            lb[q] = la[q];
+            if (k <= K || k >= N - K) {
+              if (f == 2 || f == 7) la[q] = s0[gi];
+              else if (f == 3) la[q] = jh[gi];
+              else if (f == 4 || f == 5) la[q] = s1[gi];
+              if (f == 5) lb[q] = s2[gi];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < LB; ++q) {
+            const int m = m0 + q;
+            const int k = t + TT * m;
+            if (!(k <= K || k >= N - K)) continue;
+            const int my = k <= K ? k : k - N;
+            const T ky = T(g.kscale) * T(my);
+            const size_t gi = colbase + (k <= K ? k : k - N + Ny);
+            const bool in_test = mx * mx + my * my <= d.test_m2max;
+            const C X = col_ok ? x[m] : mk<C>(T(0), T(0));
+            if (f == 0) {
+              jh[gi] = X;
+            } else if (f == 1) {
+              s0[gi] = X;
+            } else if (f == 2) {
+              const C D = cadd(la[q], cmul_ik(X, ky));
+              dh[gi] = D;
+              s1[gi] = in_test ? mk<C>(-D.x, -D.y) : mk<C>(T(0), T(0));
+            } else if (f == 3) {
+              s2[gi] = in_test ? csub(X, la[q]) : X;
+            } else if (f == 4) {
+              s1[gi] = cadd(la[q], cscale(X, T(d.rpow)));
+            } else if (f == 6) {
+              s0[gi] = cscale(cmul_ik(X, ky), T(d.inv_eta));
+            } else if (f == 7) {
+              reinterpret_cast<C*>(d.bh)[gi] = csub(la[q], cscale(cmul_ik(X, kxv), T(d.inv_eta)));
+            } else if (col_ok) {
+              const C M = cadd(la[q], cscale(cmul_ik(X, ky), T(d.rpow)));
+              const C H = lb[q];
+              const T wgt = mx == 0 ? T(1) : T(2);
+              acc_hm.add_prod(wgt * H.x, M.x);
+              acc_hm.add_prod(wgt * H.y, M.y);
+              acc_mm.add_prod(wgt * M.x, M.x);
+              acc_mm.add_prod(wgt * M.y, M.y);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < E::EL && !LEAN; ++m) {
         const int k = t + TT * m;
         const int my = k <= K ? k : k - N;
         const T ky = T(g.kscale) * T(my);
@@ -774,13 +849,13 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
 template <typename T, int N>
 cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, const TmaSet& tm, cudaStream_t st) {
   using Cfg = fast::ColCfg<N>;
-  const size_t smem = (size_t)3 * fast::col_stage_bytes<T, N>() + 1024;
   const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);
   const int grid = g.Kcp / Cfg::W;
   cudaError_t e = cudaSuccess;
 #define QG_COL_CASE(P)                                                                                   \
   case P: {                                                                                              \
     auto k = fast::col_fast_kernel<T, N, P>;                                                            \
+    const size_t smem = (size_t)(fast::col_lean<T, P>() ? 2 : 3) * fast::col_stage_bytes<T, N>() + 1024; \
     static unsigned long long attr_done = 0ull;                                                         \
     int dev_ = 0;                                                                                        \
     cudaGetDevice(&dev_);                                                                                \

@@ -203,6 +203,7 @@ struct qg_handle {
   void* ws = nullptr;
   void* ws2 = nullptr;  // second stage-state array (stages alternate between ws and ws2)
   void* jh = nullptr;
+  void* red_scr[3] = {nullptr, nullptr, nullptr};  // Germano reduction scratch (FP32 register-resident kernels)
   void* dh = nullptr;
   void* X[kMaxIn] = {};
   void* Y[kMaxY] = {};
@@ -438,6 +439,7 @@ ColDesc col_base(qg_handle* h) {
   d.ws = h->ws;
   d.ws_out = h->ws;
   d.jh = h->jh;
+  for (int i = 0; i < 3; ++i) d.scr[i] = h->red_scr[i];
   d.dh = h->dh;
   d.dt = h->par.dt;
   d.beta = h->beta;
@@ -1473,6 +1475,7 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
   if (!rc) rc = dalloc(h, &h->ws2, spec_bytes);
   if (!rc && h->dynamic) rc = dalloc(h, &h->jh, spec_bytes);
   if (!rc && h->dynamic) rc = dalloc(h, &h->dh, spec_bytes);
+  for (int i = 0; i < 3 && !rc && h->dynamic && h->fast && h->fp32; ++i) rc = dalloc(h, &h->red_scr[i], spec_bytes);
   for (int i = 0; i < h->nin && !rc; ++i) rc = dalloc(h, &h->X[i], mixed_bytes);
   const int ny = h->nout > 2 ? h->nout : 2;
   for (int i = 0; i < ny && !rc; ++i) rc = dalloc(h, &h->Y[i], mixed_bytes);

@@ -137,6 +137,8 @@ struct ColDesc {
   void* ws_out;    // RK stage state written when store_ws (a different array, so split passes never race)
   void* jh;        // dynamic closures: stored J_hat
   void* dh;        // dynamic closures: stored D_hat
+  void* scr[3];    // dynamic closures, FP32 register-resident kernels: the Germano reduction's cross-field
+                   // values (spectral layout, kept modes only)
   int use_ws;      // the stage input is ws (else w0)
   int store_ws, store_w0;
   int zero_mean;   // set the (0,0) mode to zero before storing / deriving
