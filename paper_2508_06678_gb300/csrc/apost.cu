@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -552,13 +553,49 @@ struct Timer {
   }
 };
 
+// Per-device facts the launch configuration needs, queried once: the SM count and the resident
+// CTAs per SM of each pairs-kernel variant ([FP64][16-byte staging]).
+struct DevFacts {
+  bool ready = false;
+  int nsm = 1;
+  int occ[2][2] = {{1, 1}, {1, 1}};
+};
+
+template <typename K>
+int pair_occupancy(K kernel) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kPairThreads, 0) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return occ;
+}
+
+const DevFacts& dev_facts(int dev) {
+  static std::mutex mu;
+  static std::vector<DevFacts> facts;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)facts.size() <= dev) facts.resize(dev + 1);
+  DevFacts& f = facts[dev];
+  if (!f.ready) {
+    if (cudaDeviceGetAttribute(&f.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || f.nsm < 1) f.nsm = 1;
+    f.occ[0][0] = pair_occupancy(series_pairs_kernel<float, false>);
+    f.occ[0][1] = pair_occupancy(series_pairs_kernel<float, true>);
+    f.occ[1][0] = pair_occupancy(series_pairs_kernel<double, false>);
+    f.occ[1][1] = pair_occupancy(series_pairs_kernel<double, true>);
+    f.ready = true;
+  }
+  return f;
+}
+
 template <typename T>
 cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t npts, int lag_min, int nlag,
                         cudaStream_t st, Scratch& S, Timer& tm, double* d_dist, double* d_pcc, double* d_mean,
                         int* d_phase) {
-  int dev = 0, nsm = 1;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const DevFacts& facts = dev_facts(dev);
+  const int nsm = facts.nsm;
   // moments: (snapshot, slice) CTAs, slices of at most 64 KB (the slices resident at once fit in L2, so
   // each CTA's second read of its slice hits it), at least four CTAs per SM, at least 1024 points a slice
   const int nsnap = n_les + n_ff;
@@ -590,8 +627,7 @@ cudaError_t run_compare(const T* les, int n_les, const T* ff, int n_ff, int64_t 
   const int64_t rounds = (npts + P - 1) / P;
   const int64_t tiles = (int64_t)tiles_t * tiles_l;
   // about three waves of resident pair CTAs (tiles at the edges of the pair grid finish early)
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pairs, kPairThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int occ = facts.occ[sizeof(T) == 8][vec];
   int64_t nchunk = (3 * (int64_t)occ * nsm + tiles - 1) / tiles;
   const int64_t per_chunk_bytes = 16 * (int64_t)n_ff * nlag;
   const int64_t cap = (int64_t)kPartialBytes / per_chunk_bytes;
@@ -671,9 +707,11 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
     df = b;
   }
   const size_t npair = (size_t)n_ff_snap * nlag;
-  double* d_out = static_cast<double*>(S.get(sizeof(double) * (2 * npair + nlag)));
-  int* d_phase = static_cast<int*>(S.get(3 * sizeof(int)));  // phase, found, phase CTAs done
-  if (!d_out || !d_phase) return fail(QG_ERR_OOM, "qg_series_compare: device allocation failed");
+  // results: dist, pcc, mean_dist (doubles), then phase, found and the phase kernel's CTA counter (ints)
+  const size_t nres = 2 * npair + nlag;
+  double* d_out = static_cast<double*>(S.get(sizeof(double) * nres + 4 * sizeof(int)));
+  if (!d_out) return fail(QG_ERR_OOM, "qg_series_compare: device allocation failed");
+  int* d_phase = reinterpret_cast<int*>(d_out + nres);
   Timer tm;
   tm.start(kernel_ms != nullptr, st);
   cudaError_t e = dtype == QG_FP32
@@ -688,18 +726,20 @@ extern "C" int qg_series_compare(const void* les, int32_t n_les_snap, const void
     snprintf(msg, sizeof(msg), "qg_series_compare: %s", cudaGetErrorString(e));
     return fail(e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA, msg);
   }
-  std::vector<double> h(2 * npair + nlag);
-  int hp[2] = {0, 0};
-  e = cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hp, d_phase, sizeof(hp), cudaMemcpyDeviceToHost, st);
+  // one copy back: the doubles and the two result ints behind them
+  std::vector<unsigned char> hb(sizeof(double) * nres + 2 * sizeof(int));
+  e = cudaMemcpyAsync(hb.data(), d_out, hb.size(), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "qg_series_compare: %s", cudaGetErrorString(e));
     return fail(QG_ERR_CUDA, msg);
   }
-  std::copy(h.begin(), h.begin() + npair, dist);
-  if (pcc) std::copy(h.begin() + npair, h.begin() + 2 * npair, pcc);
-  if (mean_dist) std::copy(h.begin() + 2 * npair, h.end(), mean_dist);
+  const double* h = reinterpret_cast<const double*>(hb.data());
+  int hp[2];
+  memcpy(hp, hb.data() + sizeof(double) * nres, sizeof(hp));
+  std::copy(h, h + npair, dist);
+  if (pcc) std::copy(h + npair, h + 2 * npair, pcc);
+  if (mean_dist) std::copy(h + 2 * npair, h + nres, mean_dist);
   if (phase) *phase = hp[0];
   if (kernel_ms) tm.read(kernel_ms);
   if (!hp[1]) return fail(QG_ERR_ARG, "qg_series_compare: no lag in the range pairs any two snapshots");
