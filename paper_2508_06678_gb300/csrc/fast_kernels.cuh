@@ -15,7 +15,7 @@
 #define QG_COL_MINB 2
 #endif
 #ifndef QG_COL_MINB_REDUCE
-#define QG_COL_MINB_REDUCE 3
+#define QG_COL_MINB_REDUCE 2
 #endif
 #ifndef QG_LEAN_BATCH
 #define QG_LEAN_BATCH 4
@@ -57,16 +57,15 @@ template <int N> struct ColCfg {
   static constexpr int BR = fast_box_rows(N);  // rows per TMA box
   static constexpr int NBOX = N / BR;
 };
-// The FP32 Germano reduction keeps its cross-field sums in global scratch rather than registers and
-// stages its tiles through one buffer, so three CTAs fit on an SM and all K + 1 columns run in one wave.
-template <typename T, int OP> __host__ __device__ constexpr bool col_lean() {
-  return OP == CO_DYN_REDUCE && sizeof(T) == 4;
-}
 // bytes of one shared-memory stage: a dense W x N tile for TMA, or W padded exchange columns
 template <typename T, int N> __host__ __device__ constexpr int col_stage_bytes() {
   constexpr int dense = N * ColCfg<N>::W * 2 * (int)sizeof(T);
   constexpr int padded = ColCfg<N>::W * ColCfg<N>::CP * 2 * (int)sizeof(T);
   return ((dense > padded ? dense : padded) + 1023) / 1024 * 1024;
+}
+// three lean Germano-reduction CTAs (exchange buffer + one stage + alignment slack each) fit in shared memory
+template <typename T, int N> constexpr bool lean_fits() {
+  return sizeof(T) == 4 && 3 * (2 * col_stage_bytes<T, N>() + 2048) <= 227 * 1024;
 }
 // bounded device waits: about one second of SM clocks
 constexpr long long kWaitCycles = 2000000000LL;
@@ -326,8 +325,11 @@ template <> struct FInvK2<float> {
 #endif
 constexpr int kStateBatch = QG_STATE_BATCH;
 
-template <typename T, int N, int OP>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_kernel(
+// LEAN (the FP32 Germano reduction only): the cross-field values go to global scratch rather than registers
+// and the tiles come through one TMA stage, so three CTAs fit on an SM.  The launcher picks it when that turns
+// a partial second wave of column CTAs into one wave.
+template <typename T, int N, int OP, bool LEAN = false>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col) col_fast_kernel(
     Geom g, ColDesc d, const cplx_t<T>* __restrict__ tw, const __grid_constant__ TmaSet tm) {
   using E = Eng<T, N>;
   using C = cplx_t<T>;
@@ -348,7 +350,6 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, Occ<T, OP>::col) col_fast_
   __shared__ __align__(8) uint64_t mbar[2];
   // TMA tiles need 128-byte aligned shared addresses: align the base explicitly (1 KB slack is allocated)
   unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr bool LEAN = col_lean<T, OP>();
   constexpr int NSTG = LEAN ? 1 : 2;  // TMA stages of the forward fields
   C* xbuf = reinterpret_cast<C*>(sbase);
   C* stage[2] = {reinterpret_cast<C*>(sbase + SB), reinterpret_cast<C*>(sbase + (NSTG == 2 ? 2 : 1) * SB)};
@@ -846,42 +847,66 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
   return cudaGetLastError();
 }
 
+template <typename T, int N, int P, bool LEAN>
+cudaError_t launch_col_one(const Geom& g, const ColDesc& d, const cplx_t<T>* twp, const TmaSet& tm, int grid,
+                           cudaStream_t st) {
+  using Cfg = fast::ColCfg<N>;
+  auto k = fast::col_fast_kernel<T, N, P, LEAN>;
+  const size_t smem = (size_t)(LEAN ? 2 : 3) * fast::col_stage_bytes<T, N>() + 1024;
+  static unsigned long long attr_done = 0ull;  // the shared-memory attribute is set once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(attr_done >> dev & 1ull)) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_done |= 1ull << dev;
+  }
+  k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp, tm);
+  return cudaGetLastError();
+}
+
+// SMs of the current device, queried once per device
+inline int device_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64) return 1;
+  if (!sms[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    sms[dev] = n;
+  }
+  return sms[dev];
+}
+
 template <typename T, int N>
 cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, const TmaSet& tm, cudaStream_t st) {
   using Cfg = fast::ColCfg<N>;
   const auto* twp = reinterpret_cast<const cplx_t<T>*>(tw);
   const int grid = g.Kcp / Cfg::W;
-  cudaError_t e = cudaSuccess;
-#define QG_COL_CASE(P)                                                                                   \
-  case P: {                                                                                              \
-    auto k = fast::col_fast_kernel<T, N, P>;                                                            \
-    const size_t smem = (size_t)(fast::col_lean<T, P>() ? 2 : 3) * fast::col_stage_bytes<T, N>() + 1024; \
-    static unsigned long long attr_done = 0ull;                                                         \
-    int dev_ = 0;                                                                                        \
-    cudaGetDevice(&dev_);                                                                                \
-    if (dev_ >= 64 || !(attr_done >> dev_ & 1ull)) {                                                     \
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
-      if (e != cudaSuccess) return e;                                                                    \
-      if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
-    }                                                                                                    \
-    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp, tm);                                                 \
-    break;                                                                                               \
-  }
+#define QG_COL_CASE(P) \
+  case P:              \
+    return launch_col_one<T, N, P, false>(g, d, twp, tm, grid, st);
   switch (d.op) {
     QG_COL_CASE(CO_DERIVE)
     QG_COL_CASE(CO_STAGE_STATIC)
-    QG_COL_CASE(CO_DYN_REDUCE)
     QG_COL_CASE(CO_DYN_COMBINE)
     QG_COL_CASE(CO_CURL)
     QG_COL_CASE(CO_FORWARD)
     QG_COL_CASE(CO_AB2CN)
     QG_COL_CASE(CO_AB2CN_COMBINE)
     QG_COL_CASE(CO_AB2CN_FINAL)
+    case CO_DYN_REDUCE:
+      if constexpr (fast::lean_fits<T, N>()) {
+        // the lean form when the columns need more than one wave at two CTAs per SM but one at three
+        if (d.scr[0] && d.scr[1] && d.scr[2] && grid > 2 * device_sms() && grid <= 3 * device_sms())
+          return launch_col_one<T, N, CO_DYN_REDUCE, true>(g, d, twp, tm, grid, st);
+      }
+      return launch_col_one<T, N, CO_DYN_REDUCE, false>(g, d, twp, tm, grid, st);
     default:
       return cudaErrorInvalidValue;
   }
 #undef QG_COL_CASE
-  return cudaGetLastError();
 }
 
 #define QG_INSTANTIATE_FAST(N)                                                                          \
