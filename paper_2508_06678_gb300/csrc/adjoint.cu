@@ -32,6 +32,7 @@ constexpr int kThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_combine_kernel(Geom g, AdjCombine a) {
+  pdl_enter();
   using C = cplx_t<T>;
   const size_t total = (size_t)g.Kcp * g.SP;
   C* out = reinterpret_cast<C*>(a.out);
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) adj_combine_kernel(Geom g, AdjCombin
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_products_kernel(size_t count, AdjProducts a) {
+  pdl_enter();
   auto L = [](const void* p, size_t i) { return reinterpret_cast<const T*>(p)[i]; };
   auto S = [&](int k, size_t i, T v) { reinterpret_cast<T*>(a.out[k])[i] = v; };
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) adj_products_kernel(size_t count, Ad
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_scale_kernel(size_t count, const void* f, const void* x0, T s0,
                                                              void* out0, const void* x1, T s1, void* out1) {
+  pdl_enter();
   const T* F = reinterpret_cast<const T*>(f);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     reinterpret_cast<T*>(out0)[i] = s0 * F[i] * reinterpret_cast<const T*>(x0)[i];
@@ -153,6 +156,7 @@ __device__ double adj_block_sum(double v, double* red) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_spec_dot_kernel(Geom g, const void* A, const void* B,
                                                                 double* partials) {
+  pdl_enter();
   __shared__ double red[kThreads / 32];
   const size_t total = (size_t)g.Kcp * g.SP;
   double s = 0.0;
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(kThreads) adj_spec_dot_kernel(Geom g, const vo
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_phys_dot_kernel(size_t count, const void* X, const void* Y,
                                                                 const void* Z, double* partials) {
+  pdl_enter();
   __shared__ double red[kThreads / 32];
   const T* x = reinterpret_cast<const T*>(X);
   const T* y = reinterpret_cast<const T*>(Y);
@@ -183,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) adj_phys_dot_kernel(size_t count, co
 
 __global__ void adj_scalar_kernel(int op, const double* x0, const double* x1, const double* x2, double n2,
                                   double* out) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   if (op == AS_COEFF) {
     out[0] = x1[0] > 0.0 ? fmax(0.0, x0[0] / x1[0]) : 0.0;
@@ -193,12 +199,12 @@ __global__ void adj_scalar_kernel(int op, const double* x0, const double* x1, co
 
 cudaError_t launch_adj_scalar(int op, const double* x0, const double* x1, const double* x2, double n2, double* out,
                               cudaStream_t st) {
-  adj_scalar_kernel<<<1, 32, 0, st>>>(op, x0, x1, x2, n2, out);
-  return cudaGetLastError();
+  return launch_pdl(true, adj_scalar_kernel, dim3(1), dim3(32), 0, st, op, x0, x1, x2, n2, out);
 }
 
 // out[0] = scale * sum of the partials, in a fixed order
 __global__ void adj_finish_kernel(const double* partials, int n, double scale, double* out) {
+  pdl_enter();
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += 32) s += partials[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -214,37 +220,39 @@ unsigned grid_for(size_t count) {
 
 template <typename T>
 cudaError_t launch_adj_combine(const Geom& g, const AdjCombine& a, cudaStream_t st) {
-  adj_combine_kernel<T><<<grid_for((size_t)g.Kcp * g.SP), kThreads, 0, st>>>(g, a);
-  return cudaGetLastError();
+  return launch_pdl(true, adj_combine_kernel<T>, dim3(grid_for((size_t)g.Kcp * g.SP)), dim3(kThreads), 0, st, g, a);
 }
 
 template <typename T>
 cudaError_t launch_adj_products(size_t count, const AdjProducts& a, cudaStream_t st) {
-  adj_products_kernel<T><<<grid_for(count), kThreads, 0, st>>>(count, a);
-  return cudaGetLastError();
+  return launch_pdl(true, adj_products_kernel<T>, dim3(grid_for(count)), dim3(kThreads), 0, st, count, a);
 }
 
 template <typename T>
 cudaError_t launch_adj_scale(size_t count, const void* f, const void* x0, double s0, void* out0, const void* x1,
                              double s1, void* out1, cudaStream_t st) {
-  adj_scale_kernel<T><<<grid_for(count), kThreads, 0, st>>>(count, f, x0, T(s0), out0, x1, T(s1), out1);
-  return cudaGetLastError();
+  return launch_pdl(true, adj_scale_kernel<T>, dim3(grid_for(count)), dim3(kThreads), 0, st, count, f, x0, T(s0), out0, x1,
+                    T(s1), out1);
 }
 
 template <typename T>
 cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, double scale, double* partials,
                                 double* out, cudaStream_t st) {
-  adj_spec_dot_kernel<T><<<kAdjDotBlocks, kThreads, 0, st>>>(g, A, B, partials);
-  adj_finish_kernel<<<1, 32, 0, st>>>(partials, kAdjDotBlocks, scale, out);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(true, adj_spec_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, g, A, B,
+                                   partials);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(true, adj_finish_kernel, dim3(1), dim3(32), 0, st, (const double*)partials, (int)kAdjDotBlocks, scale,
+                    out);
 }
 
 template <typename T>
 cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, double scale,
                                 double* partials, double* out, cudaStream_t st) {
-  adj_phys_dot_kernel<T><<<kAdjDotBlocks, kThreads, 0, st>>>(count, X, Y, Z, partials);
-  adj_finish_kernel<<<1, 32, 0, st>>>(partials, kAdjDotBlocks, scale, out);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(true, adj_phys_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, count, X, Y,
+                                   Z, partials);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(true, adj_finish_kernel, dim3(1), dim3(32), 0, st, (const double*)partials, (int)kAdjDotBlocks, scale,
+                    out);
 }
 
 #define QG_ADJ_INST(T)                                                                                         \

@@ -214,6 +214,7 @@ __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, c
 template <typename T, int N, int PROG>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kernel(Geom g, RowDesc d,
                                                                        const cplx_t<T>* __restrict__ tw) {
+  pdl_enter();
   using E = Eng<T, N>;
   using C = cplx_t<T>;
   constexpr int TT = E::TT;
@@ -331,6 +332,7 @@ constexpr int kStateBatch = QG_STATE_BATCH;
 template <typename T, int N, int OP, bool LEAN = false>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col) col_fast_kernel(
     Geom g, ColDesc d, const cplx_t<T>* __restrict__ tw, const __grid_constant__ TmaSet tm) {
+  pdl_enter();
   using E = Eng<T, N>;
   using C = cplx_t<T>;
   constexpr int W = ColCfg<N>::W;
@@ -829,7 +831,8 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
       if (e != cudaSuccess) return e;                                                                    \
       if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
     }                                                                                                    \
-    k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp);                                                     \
+    e = launch_pdl(d.pdl != 0, k, dim3(grid), dim3(Cfg::THREADS), smem, st, g, d, twp);                \
+    if (e != cudaSuccess) return e;                                                                      \
     break;                                                                                               \
   }
   switch (d.prog) {
@@ -861,8 +864,7 @@ cudaError_t launch_col_one(const Geom& g, const ColDesc& d, const cplx_t<T>* twp
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_done |= 1ull << dev;
   }
-  k<<<grid, Cfg::THREADS, smem, st>>>(g, d, twp, tm);
-  return cudaGetLastError();
+  return launch_pdl(d.pdl != 0, k, dim3(grid), dim3(Cfg::THREADS), smem, st, g, d, twp, tm);
 }
 
 // SMs of the current device, queried once per device

@@ -762,6 +762,7 @@ int adj_alloc(qg_handle* h) {
 // spectral band (T F[f], mean removed if asked) of a physical field
 int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   RowDesc r{};
+  r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
   r.prog = RP_COPY;
   r.nin = 1;
   r.nout = 1;
@@ -771,6 +772,7 @@ int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   int rc = run_row(h, r, QG_K_ADJ_ROW, false);
   if (rc) return rc;
   ColDesc c = col_base(h);
+  c.pdl = 1;
   c.op = CO_FORWARD;
   c.nfwd = 1;
   c.fin[0] = h->adj_M[0];
@@ -789,6 +791,7 @@ int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::in
   for (size_t i = 0; i < p.size() && !rc; i += 2) {
     const bool two = i + 1 < p.size();
     RowDesc r{};
+  r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
     r.prog = RP_COPY;
     r.nin = 1;
     r.nout = two ? 2 : 1;
@@ -800,6 +803,7 @@ int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::in
     rc = run_row(h, r, QG_K_ADJ_ROW, false);
     for (int k = 0; k < (two ? 2 : 1) && !rc; ++k) {
       ColDesc c = col_base(h);
+  c.pdl = 1;
       c.op = CO_FORWARD;
       c.nfwd = 1;
       c.fin[0] = h->adj_M[k];
@@ -816,6 +820,7 @@ int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::in
 // state: one derive pass, then row passes in pairs
 int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, std::initializer_list<void*> P) {
   ColDesc c = col_base(h);
+  c.pdl = 1;
   c.op = CO_DERIVE;
   c.w0 = const_cast<void*>(S);
   c.nder = 0;
@@ -829,6 +834,7 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
   for (size_t i = 0; i < dst.size() && !rc; i += 2) {
     const bool two = i + 1 < dst.size();
     RowDesc r{};
+  r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
     r.prog = RP_COPY;
     r.nin = two ? 2 : 1;
     r.nout = 1;

@@ -14,6 +14,9 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+
+#include <utility>
 
 namespace qg {
 
@@ -122,6 +125,7 @@ struct RowDesc {
   const void* factor;  // RP_SCALE: physical factor field
   int check_finite;    // set *flag if a product is not finite
   int* flag;
+  int pdl;             // host side: launch with programmatic stream serialisation
 };
 
 struct ColDesc {
@@ -169,6 +173,7 @@ struct ColDesc {
   const void* visc_x;  // exp(-nu kx^2 dt), per m_x
   const void* visc_y;  // exp(-nu ky^2 dt), per r
   double visc_mu;      // exp(-mu dt)
+  int pdl;             // host side: launch with programmatic stream serialisation
   int* flag;           // stop flag checked at entry (NULL: always run)
   int* err;            // status bits raised by bounded waits that give up (NULL: not reported)
 };
@@ -177,6 +182,39 @@ struct ColDesc {
 // FP64; FP32 fields use error-free transformations (TwoProduct by FMA,
 // TwoSum) so the per-thread partial carries about twice FP32 precision
 // before it joins the FP64 cross-thread reduction.
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be scheduled while the kernel before
+// it on the stream is still finishing: it first waits here, before any memory access, until that kernel has
+// completed and its writes are visible, then lets the next kernel be scheduled.  Launched without the
+// attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// programmatic launches are allowed unless QG_NO_PDL is set in the environment (read once)
+inline bool pdl_enabled() {
+  static const bool on = getenv("QG_NO_PDL") == nullptr;
+  return on;
+}
+
+// k<<<grid, block, smem, st>>>(args...), with programmatic stream serialisation when pdl is set (k must call
+// pdl_enter() first).  The adjoint's chains of small launches gain from it; the forward step's graph measured
+// slower with it, so its launches leave it off.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl && pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 template <typename T> struct GermanoAcc;
 template <> struct GermanoAcc<double> {
   double s = 0.0;
