@@ -4,6 +4,8 @@
 // one translation unit per grid size.
 #pragma once
 
+#include <atomic>
+
 #include "fast.cuh"
 #include "qg_kernels.h"
 #include "tma.cuh"
@@ -347,11 +349,11 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
   // shared memory: exchange buffer | stage 0 | stage 1.  A stage receives a
   // field's dense W x N tile by TMA, then serves as the FFT's second exchange
   // buffer, and in the inverse phase holds the dense output tile for the TMA store.
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_col[];
   __shared__ double red[2][32];
   __shared__ __align__(8) uint64_t mbar[2];
   // TMA tiles need 128-byte aligned shared addresses: align the base explicitly (1 KB slack is allocated)
-  unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_col) + 1023) & ~uintptr_t(1023));
   constexpr int NSTG = LEAN ? 1 : 2;  // TMA stages of the forward fields
   C* xbuf = reinterpret_cast<C*>(sbase);
   C* stage[2] = {reinterpret_cast<C*>(sbase + SB), reinterpret_cast<C*>(sbase + (NSTG == 2 ? 2 : 1) * SB)};
@@ -867,18 +869,18 @@ cudaError_t launch_col_one(const Geom& g, const ColDesc& d, const cplx_t<T>* twp
   return launch_pdl(d.pdl != 0, k, dim3(grid), dim3(Cfg::THREADS), smem, st, g, d, twp, tm);
 }
 
-// SMs of the current device, queried once per device
+// SMs of the current device, queried once per device (concurrent first calls store the same value)
 inline int device_sms() {
-  static int sms[64] = {};
+  static std::atomic<int> sms[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 64) return 1;
-  if (!sms[dev]) {
-    int n = 0;
+  if (dev < 0 || dev >= 64) return 1;
+  int n = sms[dev].load(std::memory_order_relaxed);
+  if (!n) {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-    sms[dev] = n;
+    sms[dev].store(n, std::memory_order_relaxed);
   }
-  return sms[dev];
+  return n;
 }
 
 template <typename T, int N>
