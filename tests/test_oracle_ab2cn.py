@@ -118,3 +118,33 @@ def test_ab2cn_full_configuration_runs_and_keeps_band():
               chi=island_mask(n, radius=0.8), chi_s=sponge_mask(n), closure=O.Closure(O.DLEITH))
     assert np.all(np.isfinite(out)) and out[0, 0] == 0
     assert np.all(out[ops.T == 0] == 0)
+
+
+@pytest.mark.parametrize("r,grows", [(0.5, False), (0.9, False), (1.2, True), (2.0, True)])
+def test_explicit_penalisation_needs_eta_above_dt(r, grows):
+    """Sec. II-E: treated explicitly, the penalisation is stable only for eta > dt.  With chi = 1 (and U = 0)
+    every mode obeys dw/dt = -w/eta; AB2 gives w_{n+1} = (1 - 3r/2) w_n + r/2 w_{n-1}, r = dt/eta, whose roots
+    leave the unit circle for r > 1 (at r = 1.2 the larger one is 1.272, at r = 0.9 it is 0.868).  The RK3
+    split's exact implicit sub-step damps the same mode by exactly exp(-r) per step at any eta."""
+    n, dt, steps = 16, 1e-3, 200
+    eta = dt / r
+    ops = O.Ops(n)
+    X, Y = grid(n)
+    w = np.sin(X + Y)
+    wh0 = O.project(ops, w)
+    idx = (1, 1)  # the k = (1, 1) mode of the half spectrum
+    chi = np.ones((n, n))
+    with np.errstate(over="ignore", invalid="ignore"):  # the unstable runs overflow
+        ab2 = run(ops, w, steps, 0.0, 0.0, O.Params(dt=dt, nu=0.0, mu=0.0, eta=eta, scheme=O.AB2CN), chi=chi)
+        growth = abs(ab2[idx]) / abs(wh0[idx])
+    if grows:
+        assert not np.isfinite(growth) or growth > 1e10
+    else:
+        assert growth < 1.0
+    # the scalar recurrence written out here agrees where it stays finite
+    if not grows:
+        expected = scalar_ab2cn(wh0[idx], steps, dt, 0.0, -1.0 / eta)
+        assert abs(ab2[idx] - expected) <= 1e-12 * abs(wh0[idx])
+    exact = run(ops, w, steps, 0.0, 0.0, O.Params(dt=dt, nu=0.0, mu=0.0, eta=eta), chi=chi)
+    assert abs(exact[idx]) / abs(wh0[idx]) == pytest.approx(math.exp(-r * steps), rel=1e-10)
+
