@@ -48,7 +48,7 @@ extern "C" {
 #define QG_ERR_NONFINITE (-3) /* a non-finite value appeared in the state; stepping stopped */
 #define QG_ERR_OOM (-4)       /* device allocation failed */
 #define QG_ERR_TIMEOUT (-5)   /* a bounded device wait gave up (an async copy never arrived) */
-#define QG_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve (e.g. shared memory) */
+#define QG_ERR_UNSUPPORTED (-6) /* valid request the library cannot serve on this device (e.g. shared memory) */
 
 /* Working precision of the device fields. */
 #define QG_FP64 0
