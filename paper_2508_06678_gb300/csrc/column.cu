@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           else slotA[e] = csub(slotA[e], cscale(cmul_ik(X, kx), T(d.inv_eta)));
           break;
         }
+        case CO_FORWARD2:
+          if (f == 0) slotA[e] = X;
+          else slotB[e] = X;
+          break;
         default:  // CO_FORWARD
           slotA[e] = X;
           break;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
         case CO_AB2CN_FINAL:
           wn = csub(reinterpret_cast<const C*>(d.wss)[gi], slotA[e]);
           break;
-        default:  // CO_CURL, CO_FORWARD
+        default:  // CO_CURL, CO_FORWARD, CO_FORWARD2
           wn = slotA[e];
           break;
       }
@@ -305,6 +309,12 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
       if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
       if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
       if (d.store_w0) w0[gi] = wn;
+      if (d.op == CO_FORWARD2) {  // the second field, treated like the first
+        C wb = slotB[e];
+        if (d.viscous) wb = cscale(wb, vx[mx] * vy[r] * vmu);
+        if (d.zero_mean && mx == 0 && my == 0) wb = mk<C>(T(0), T(0));
+        reinterpret_cast<C*>(d.w0b)[gi] = wb;
+      }
     }
     slotA[e] = wn;
   }

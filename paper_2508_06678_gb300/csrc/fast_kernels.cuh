@@ -41,7 +41,7 @@ template <int N> struct RowCfg {
 template <typename T, int OP = -1> struct Occ {
   static constexpr int row = QG_ROW_MINB;
   static constexpr int col = OP == CO_DYN_REDUCE ? QG_COL_MINB_REDUCE
-                             : (OP == CO_FORWARD || OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
+                             : (OP == CO_FORWARD || OP == CO_FORWARD2 || OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
                              : OP == CO_CURL    ? QG_COL_MINB_CURL
                                                 : QG_COL_MINB;
 };
@@ -542,6 +542,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
           else if (f < d.nst) B[m] = (f == 1) ? X : cadd(B[m], cmul_ik(X, ky));
           else if (f == d.nst) A[m] = cadd(A[m], cscale(cmul_ik(X, ky), T(d.inv_eta)));
           else A[m] = csub(A[m], cscale(cmul_ik(X, kxv), T(d.inv_eta)));
+        } else if constexpr (OP == CO_FORWARD2) {
+          if (f == 0) A[m] = X;
+          else B[m] = X;
         } else {  // CO_FORWARD, CO_AB2CN_FINAL
           A[m] = X;
         }
@@ -720,6 +723,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
           if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
           if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
           if (d.store_w0) w0[gi] = wn;
+          if constexpr (OP == CO_FORWARD2) {  // the second field, treated like the first
+            C wb = B[m];
+            if (d.viscous) wb = cscale(wb, vf[q]);
+            if (d.zero_mean && mx == 0 && my == 0) wb = mk<C>(T(0), T(0));
+            reinterpret_cast<C*>(d.w0b)[gi] = wb;
+          }
         }
         A[m] = wn;
       }
@@ -897,6 +906,7 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, con
     QG_COL_CASE(CO_DYN_COMBINE)
     QG_COL_CASE(CO_CURL)
     QG_COL_CASE(CO_FORWARD)
+    QG_COL_CASE(CO_FORWARD2)
     QG_COL_CASE(CO_AB2CN)
     QG_COL_CASE(CO_AB2CN_COMBINE)
     QG_COL_CASE(CO_AB2CN_FINAL)

@@ -801,17 +801,19 @@ int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::in
     r.out[0] = h->adj_M[0];
     r.out[1] = h->adj_M[1];
     rc = run_row(h, r, QG_K_ADJ_ROW, false);
-    for (int k = 0; k < (two ? 2 : 1) && !rc; ++k) {
-      ColDesc c = col_base(h);
-  c.pdl = 1;
-      c.op = CO_FORWARD;
-      c.nfwd = 1;
-      c.fin[0] = h->adj_M[k];
-      c.w0 = s[i + k];
-      c.store_w0 = 1;
-      c.nder = 0;
-      rc = run_col(h, c, QG_K_ADJ_COL, false);
-    }
+    if (rc) break;
+    // one column pass per pair: the first field to s[i], the second to s[i + 1]
+    ColDesc c = col_base(h);
+    c.pdl = 1;
+    c.op = two ? CO_FORWARD2 : CO_FORWARD;
+    c.nfwd = two ? 2 : 1;
+    c.fin[0] = h->adj_M[0];
+    c.fin[1] = two ? h->adj_M[1] : nullptr;
+    c.w0 = s[i];
+    c.w0b = two ? s[i + 1] : nullptr;
+    c.store_w0 = 1;
+    c.nder = 0;
+    rc = run_col(h, c, QG_K_ADJ_COL, false);
   }
   return rc;
 }

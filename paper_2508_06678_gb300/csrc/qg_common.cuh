@@ -108,6 +108,7 @@ enum ColOp : int {
   CO_AB2CN = 6,          // forward J[, P, Q][, chi u, chi v]; CN / AB2 combine; sponge field or next state
   CO_AB2CN_COMBINE = 7,  // as CO_AB2CN from stored J, D, F_obs and the Germano partial sums
   CO_AB2CN_FINAL = 8,    // forward s = dt rate chi_s Z; w^{t+1} = w* - s
+  CO_FORWARD2 = 9,       // forward two fields: the first to w0, the second to w0b (the adjoint's paired transforms)
 };
 
 struct RowDesc {
@@ -137,6 +138,7 @@ struct ColDesc {
   void* dout[kMaxDer];
   // spectral arrays
   void* w0;        // state w^n (read; written when store_w0)
+  void* w0b;       // CO_FORWARD2: the second field's spectral band (written)
   void* ws;        // RK stage state read when use_ws
   void* ws_out;    // RK stage state written when store_ws (a different array, so split passes never race)
   void* jh;        // dynamic closures: stored J_hat
