@@ -7,6 +7,13 @@ coefficient, the viscous factor, the Brinkman and the sponge sub-steps.
 
 Prints one JSON line.  Multi-GPU (torchrun, one process per GPU) runs
 independent replicas: the step has no data-parallel split on one grid.
+
+The roofline object reports the dominant kernel class (the stage row pass)
+against the measured HBM copy peak: "achieved" / "frac" count the
+full-field round-trip bytes (every 2-D transform moves one N^2 field between
+its passes), "band_model" the arrays this design keeps (2/3 band only), and
+"step_frac" the whole step on the full-field model.  Other workloads:
+--scheme ab2cn (Eq. 4), --workload ensemble96 | adjoint256 | series512.
 """
 from __future__ import annotations
 
