@@ -49,7 +49,11 @@ derivatives of trigonometric polynomials, 3/2-rule de-aliasing equivalence,
 Jacobian antisymmetry and discrete conservation, single-mode Rossby wave
 against the RK3 stability polynomial, viscous decay, penalisation and sponge
 exponentials, nu_e >= 0, Germano coefficient against brute-force least
-squares, a priori invariances.  Parity unpinned: the absolute a priori PCC
+squares, a priori invariances; the eddy-viscosity divergence of Eq. 9 with a
+prescribed g (constant g = diffusion, single-mode closed forms), its
+enstrophy dissipation by summation by parts and its truncation; the obstacle
+and sponge forcings of Eq. 2-3 for constant masks and single-mode closed
+forms.  Parity unpinned: the absolute a priori PCC
 values of Tab. I/III (need the authors' data) and the Gaussian constant of R9.
 """
 from __future__ import annotations

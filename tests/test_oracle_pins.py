@@ -453,3 +453,139 @@ def test_pcc_properties():
     assert O.pcc(X, X) == pytest.approx(1.0, abs=1e-15)
     assert O.pcc(X, 3.0 * Y - 2.0) == pytest.approx(O.pcc(X, Y), abs=1e-14)
     assert O.pcc(X, -Y) == pytest.approx(-O.pcc(X, Y), abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# The eddy-viscosity term div(g grad w) (Eq. 9) and the forcings of Eq. 8
+# (Eq. 2, 3).  g is replaced by a prescribed field through the module's
+# eddy_scale hook, so the divergence itself is checked against closed forms.
+# --------------------------------------------------------------------------
+
+import oracle.qg as OQ
+
+
+def _prescribe_g(monkeypatch, g):
+    monkeypatch.setattr(OQ, "eddy_scale", lambda ops, wh, kind: g)
+
+
+def _half_weights(shape):
+    w = np.full(shape, 2.0)
+    w[:, 0] = 1.0
+    w[:, -1] = 1.0
+    return w
+
+
+@pytest.mark.parametrize("kind", [O.SMAG, O.LEITH])
+def test_sgs_divergence_constant_g_is_diffusion(monkeypatch, kind):
+    """g = gamma constant: div(gamma grad w) = gamma lap w, i.e. -gamma |k|^2 w_hat."""
+    n = 32
+    ops = O.Ops(n)
+    wh = O.project(ops, init_field(31, n))
+    gamma = 0.73
+    _prescribe_g(monkeypatch, np.full((n, n), gamma))
+    D = O.sgs_divergence_hat(ops, wh, kind)
+    ref = -gamma * ops.k2 * wh
+    assert np.max(np.abs(D - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("p,q", [((1, 2), (3, -1)), ((2, 0), (3, 0)), ((0, 3), (4, 0)), ((-1, 1), (2, 5))])
+def test_sgs_divergence_closed_form_single_modes(monkeypatch, p, q):
+    """g = 1 + e cos(p.x), w = cos(q.x):
+    div(g grad w) = e (p.q) sin(p.x) sin(q.x) - |q|^2 (1 + e cos(p.x)) cos(q.x).
+    Pairs p parallel and perpendicular to q fix the pairing of k_x with w_x and the sign."""
+    n = 48
+    ops = O.Ops(n)
+    X, Y = grid(n)
+    e = 0.4
+    px, py = p
+    qx, qy = q
+    ph = px * X + py * Y
+    qh = qx * X + qy * Y
+    _prescribe_g(monkeypatch, 1.0 + e * np.cos(ph))
+    wh = O.project(ops, np.cos(qh) + 0 * X * Y)
+    D = ops.inv(O.sgs_divergence_hat(ops, wh, O.LEITH))
+    ref = e * (px * qx + py * qy) * np.sin(ph) * np.sin(qh) - (qx * qx + qy * qy) * (1 + e * np.cos(ph)) * np.cos(qh)
+    assert np.max(np.abs(D - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kind", [O.SMAG, O.LEITH, O.DSMAG, O.DLEITH])
+def test_sgs_term_dissipates_enstrophy_parseval(kind):
+    """Summation by parts on the grid: sum_x w div(g grad w) = -sum_x g |grad w|^2,
+    written in the half spectrum as sum w_k Re(conj(w_hat) D_hat) / N^2."""
+    n = 48
+    ops = O.Ops(n)
+    wh = O.project(ops, init_field(32 + kind, n, k_peak=6.0))
+    D = O.sgs_divergence_hat(ops, wh, kind)
+    lhs = np.sum(_half_weights(wh.shape) * (np.conj(wh) * D).real) / n ** 2
+    g = O.eddy_scale(ops, wh, kind)
+    wx, wy = O.vorticity_gradient(ops, wh)
+    rhs = -np.sum(g * (wx * wx + wy * wy))
+    assert rhs < 0
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+@pytest.mark.parametrize("kind", [O.SMAG, O.LEITH])
+def test_sgs_divergence_is_truncated(kind):
+    """The flux divergence is a product output: zero outside the 2/3 band (R2)."""
+    n = 48
+    ops = O.Ops(n)
+    wh = O.project(ops, init_field(40, n, k_peak=12.0))
+    D = O.sgs_divergence_hat(ops, wh, kind)
+    assert np.all(D[ops.T == 0] == 0)
+    assert np.max(np.abs(D)) > 0
+
+
+def test_obstacle_forcing_constant_mask():
+    """chi = c: F_obs = -curl(c u / eta) = -(c / eta) w (the uniform inflow has no curl)."""
+    n = 32
+    ops = O.Ops(n)
+    wh = O.project(ops, init_field(41, n))
+    c, eta = 0.6, 1e-3
+    F = O.obstacle_forcing_hat(ops, wh, np.full((n, n), c), eta, U=0.8)
+    assert rel(F, -(c / eta) * wh) < 1e-14
+
+
+@pytest.mark.parametrize("p,q", [((0, 1), (3, 0)), ((1, 2), (2, -3)), ((2, 1), (0, 4))])
+def test_obstacle_forcing_closed_form(p, q):
+    """chi = 1 + e cos(p.x), w = cos(q.x) (psi = -cos(q.x)/|q|^2, u = -psi_y + U, v = psi_x):
+    -curl(chi u)/eta = -(chi w + chi_x v - chi_y u) / eta, evaluated pointwise."""
+    n = 48
+    ops = O.Ops(n)
+    X, Y = grid(n)
+    e, eta, U = 0.3, 1e-3, 0.7
+    px, py = p
+    qx, qy = q
+    q2 = qx * qx + qy * qy
+    ph = px * X + py * Y
+    qh = qx * X + qy * Y
+    chi = 1 + e * np.cos(ph) + 0 * X * Y
+    w = np.cos(qh) + 0 * X * Y
+    u = -qy * np.sin(qh) / q2 + U
+    v = qx * np.sin(qh) / q2
+    chi_x = -e * px * np.sin(ph)
+    chi_y = -e * py * np.sin(ph)
+    ref = -(chi * w + chi_x * v - chi_y * u) / eta
+    F = ops.inv(O.obstacle_forcing_hat(ops, O.project(ops, w), chi, eta, U))
+    assert np.max(np.abs(F - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_sponge_forcing_unit_mask():
+    """chi_s = 1: F_sp = -rate (w - 0) = -rate w (Eq. 3, target 0)."""
+    n = 48
+    ops = O.Ops(n)
+    rate = 50.0
+    wh = O.project(ops, init_field(42, n))
+    assert rel(O.sponge_forcing_hat(ops, wh, np.ones((n, n)), rate), -rate * wh) < 1e-14
+
+
+def test_sponge_forcing_closed_form():
+    """chi_s = 1 + e cos(p.x), w = cos(q.x): F_sp = -rate chi_s w pointwise, inside the band."""
+    n = 48
+    ops = O.Ops(n)
+    rate = 50.0
+    X, Y = grid(n)
+    chs = 1 + 0.25 * np.cos(2 * X - Y)
+    w = np.cos(3 * X + 4 * Y)
+    F = ops.inv(O.sponge_forcing_hat(ops, O.project(ops, w), chs, rate))
+    ref = -rate * chs * w
+    assert np.max(np.abs(F - ref)) < 1e-12 * np.max(np.abs(ref))
