@@ -76,6 +76,11 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
   const int nt = blockDim.x;
   const int nspec = W * Ny;
   const double ks2 = g.kscale * g.kscale;
+  // extents for the bounds-checked debug build
+  int* const st = d.err;
+  const long long n_tile = (long long)N * W, n_mixed = (long long)N * g.IP, n_spec = (long long)g.Kcp * g.SP;
+  const long long n_part = 2LL * gridDim.x;  // Germano partial sums: two per column CTA
+  (void)n_tile; (void)n_mixed; (void)n_spec; (void)n_part; (void)st;
 
   if (d.flag) {
     const int stop = __syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0);
@@ -94,47 +99,47 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
     const C* src = reinterpret_cast<const C*>(d.fin[f]);
     for (int e = tid; e < N * W; e += nt) {
       const int y = e / W, c = e - y * W;
-      tile[e] = src[(size_t)y * g.IP + c0 + c];
+      QG_ST(tile, e, n_tile, st, QG_LD(src, (long long)y * g.IP + c0 + c, n_mixed, st));
     }
-    fft_batched<C>(tile, plan, W, tw, -1);
+    fft_batched<C>(tile, plan, W, tw, -1, st);
     for (int e = tid; e < nspec; e += nt) {
       const int c = e / Ny, r = e - c * Ny;
       const int mx = c0 + c;
       const int my = my_of_r(g, r);
-      C X = tile[(size_t)row_of_r(g, r) * W + c];
+      C X = QG_LD(tile, (long long)row_of_r(g, r) * W + c, n_tile, st);
       if (mx >= g.Kc) X = mk<C>(T(0), T(0));
       const T ky = T(g.kscale) * T(my);
       const size_t gi = (size_t)mx * g.SP + r;
       switch (d.op) {
         case CO_STAGE_STATIC:
-          if (f == 0) slotA[e] = mk<C>(-X.x, -X.y);                  // -J
-          else if (f == 1) slotB[e] = X;                             // i kx F[g wx]
-          else slotB[e] = cadd(slotB[e], cmul_ik(X, ky));            // + i ky F[g wy]
+          if (f == 0) QG_ST(slotA, e, nspec, st, mk<C>(-X.x, -X.y));                  // -J
+          else if (f == 1) QG_ST(slotB, e, nspec, st, X);                             // i kx F[g wx]
+          else QG_ST(slotB, e, nspec, st, cadd(QG_LD(slotB, e, nspec, st), cmul_ik(X, ky)));            // + i ky F[g wy]
           break;
         case CO_DYN_REDUCE: {
           const bool in_test = mx * mx + my * my <= d.test_m2max;
           if (f == 0) {                                              // J
-            slotA[e] = X;
-            jh[gi] = X;
+            QG_ST(slotA, e, nspec, st, X);
+            QG_ST(jh, gi, n_spec, st, X);
           } else if (f == 1) {                                       // i kx F[g wx]
-            slotB[e] = X;
+            QG_ST(slotB, e, nspec, st, X);
           } else if (f == 2) {                                       // D = .. + i ky F[g wy]
-            const C D = cadd(slotB[e], cmul_ik(X, ky));
-            dh[gi] = D;
-            slotB[e] = in_test ? mk<C>(-D.x, -D.y) : mk<C>(T(0), T(0));   // -G D
+            const C D = cadd(QG_LD(slotB, e, nspec, st), cmul_ik(X, ky));
+            QG_ST(dh, gi, n_spec, st, D);
+            QG_ST(slotB, e, nspec, st, in_test ? mk<C>(-D.x, -D.y) : mk<C>(T(0), T(0)));   // -G D
           } else if (f == 3) {                                       // H = J~ - G J
-            slotA[e] = in_test ? csub(X, slotA[e]) : X;
+            QG_ST(slotA, e, nspec, st, in_test ? csub(X, QG_LD(slotA, e, nspec, st)) : X);
           } else if (f == 4) {                                       // M = r^p D~ - G D
-            slotB[e] = cadd(slotB[e], cscale(X, rpow));
+            QG_ST(slotB, e, nspec, st, cadd(QG_LD(slotB, e, nspec, st), cscale(X, rpow)));
           } else if (f == 6) {  // Brinkman pair of the paper's scheme: F_obs = (i ky F[chi u] - i kx F[chi v]) / eta
-            slotA[e] = cscale(cmul_ik(X, ky), T(d.inv_eta));
+            QG_ST(slotA, e, nspec, st, cscale(cmul_ik(X, ky), T(d.inv_eta)));
           } else if (f == 7) {
             const T kx = T(g.kscale) * T(mx);
-            slotA[e] = csub(slotA[e], cscale(cmul_ik(X, kx), T(d.inv_eta)));
-            reinterpret_cast<C*>(d.bh)[gi] = slotA[e];
+            QG_ST(slotA, e, nspec, st, csub(QG_LD(slotA, e, nspec, st), cscale(cmul_ik(X, kx), T(d.inv_eta))));
+            QG_ST(reinterpret_cast<C*>(d.bh), gi, n_spec, st, QG_LD(slotA, e, nspec, st));
           } else {
-            const C M = cadd(slotB[e], cscale(cmul_ik(X, ky), rpow));
-            const C H = slotA[e];
+            const C M = cadd(QG_LD(slotB, e, nspec, st), cscale(cmul_ik(X, ky), rpow));
+            const C H = QG_LD(slotA, e, nspec, st);
             const T wgt = mx == 0 ? T(1) : T(2);
             if (mx < g.Kc) {
               acc_hm.add_prod(wgt * H.x, M.x);
@@ -146,26 +151,26 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           break;
         }
         case CO_CURL:
-          if (f == 0) slotA[e] = X;                                  // u
+          if (f == 0) QG_ST(slotA, e, nspec, st, X);                                  // u
           else {
             const T kx = T(g.kscale) * T(mx);
-            slotA[e] = csub(cmul_ik(X, kx), cmul_ik(slotA[e], ky));  // i kx v - i ky u
+            QG_ST(slotA, e, nspec, st, csub(cmul_ik(X, kx), cmul_ik(QG_LD(slotA, e, nspec, st), ky)));  // i kx v - i ky u
           }
           break;
         case CO_AB2CN: {  // E = -J + C D + F_obs: slot A collects -J + F_obs, slot B collects D
           const T kx = T(g.kscale) * T(mx);
-          if (f == 0) slotA[e] = mk<C>(-X.x, -X.y);
-          else if (f < d.nst) slotB[e] = (f == 1) ? X : cadd(slotB[e], cmul_ik(X, ky));
-          else if (f == d.nst) slotA[e] = cadd(slotA[e], cscale(cmul_ik(X, ky), T(d.inv_eta)));
-          else slotA[e] = csub(slotA[e], cscale(cmul_ik(X, kx), T(d.inv_eta)));
+          if (f == 0) QG_ST(slotA, e, nspec, st, mk<C>(-X.x, -X.y));
+          else if (f < d.nst) QG_ST(slotB, e, nspec, st, (f == 1) ? X : cadd(QG_LD(slotB, e, nspec, st), cmul_ik(X, ky)));
+          else if (f == d.nst) QG_ST(slotA, e, nspec, st, cadd(QG_LD(slotA, e, nspec, st), cscale(cmul_ik(X, ky), T(d.inv_eta))));
+          else QG_ST(slotA, e, nspec, st, csub(QG_LD(slotA, e, nspec, st), cscale(cmul_ik(X, kx), T(d.inv_eta))));
           break;
         }
         case CO_FORWARD2:
-          if (f == 0) slotA[e] = X;
-          else slotB[e] = X;
+          if (f == 0) QG_ST(slotA, e, nspec, st, X);
+          else QG_ST(slotB, e, nspec, st, X);
           break;
         default:  // CO_FORWARD
-          slotA[e] = X;
+          QG_ST(slotA, e, nspec, st, X);
           break;
       }
     }
@@ -194,8 +199,8 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
         mm += __shfl_down_sync(0xffffffffu, mm, o);
       }
       if (lane == 0) {
-        d.partials[2 * blockIdx.x] = hm;
-        d.partials[2 * blockIdx.x + 1] = mm;
+        QG_ST(d.partials, 2LL * blockIdx.x, n_part, st, hm);
+        QG_ST(d.partials, 2LL * blockIdx.x + 1, n_part, st, mm);
       }
     }
     return;
@@ -207,8 +212,8 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
     if (tid < 32) {
       double a = 0.0, b = 0.0;
       for (int i = tid; i < d.npartials; i += 32) {
-        a += d.partials[2 * i];
-        b += d.partials[2 * i + 1];
+        a += QG_LD(d.partials, 2LL * i, n_part, st);
+        b += QG_LD(d.partials, 2LL * i + 1, n_part, st);
       }
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
@@ -238,24 +243,24 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
     if (mx < g.Kc) {
       switch (d.op) {
         case CO_DERIVE:
-          wn = w0[gi];
+          wn = QG_LD(w0, gi, n_spec, st);
           break;
         case CO_STAGE_STATIC:
         case CO_DYN_COMBINE: {
-          const C wz = w0[gi];
-          const C wst = d.use_ws ? ws[gi] : wz;
+          const C wz = QG_LD(w0, gi, n_spec, st);
+          const C wst = d.use_ws ? QG_LD(ws, gi, n_spec, st) : wz;
           const T ik2 = InvK2<T>::get(ks2, mx * mx + my * my);
           const C psi = mk<C>(-wst.x * ik2, -wst.y * ik2);
           const T kx = T(g.kscale) * T(mx);
           const C bv = cscale(cmul_ik(psi, kx), beta);
           C L;
           if (d.op == CO_STAGE_STATIC) {
-            L = csub(slotA[e], bv);
-            if (d.nfwd > 1) L = cadd(L, cscale(slotB[e], coeff));
+            L = csub(QG_LD(slotA, e, nspec, st), bv);
+            if (d.nfwd > 1) L = cadd(L, cscale(QG_LD(slotB, e, nspec, st), coeff));
           } else {
-            const C J = jh[gi];
+            const C J = QG_LD(jh, gi, n_spec, st);
             L = csub(mk<C>(-J.x, -J.y), bv);
-            L = cadd(L, cscale(dh[gi], coeff));
+            L = cadd(L, cscale(QG_LD(dh, gi, n_spec, st), coeff));
           }
           const C inner = cadd(wst, cscale(L, dt));
           wn = cadd(cscale(wz, a_rk), cscale(inner, b_rk));
@@ -266,15 +271,15 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           // Eq. 4: w* = ((1 + dt/2 lin) w^t + dt (3/2 E - 1/2 E_prev)) / (1 - dt/2 lin)
           C E;
           if (d.op == CO_AB2CN) {
-            E = (d.nst > 1) ? cadd(slotA[e], cscale(slotB[e], coeff)) : slotA[e];
+            E = (d.nst > 1) ? cadd(QG_LD(slotA, e, nspec, st), cscale(QG_LD(slotB, e, nspec, st), coeff)) : QG_LD(slotA, e, nspec, st);
           } else {
-            const C J = jh[gi];
-            E = cadd(mk<C>(-J.x, -J.y), cscale(dh[gi], coeff));
-            if (d.brink) E = cadd(E, reinterpret_cast<const C*>(d.bh)[gi]);
+            const C J = QG_LD(jh, gi, n_spec, st);
+            E = cadd(mk<C>(-J.x, -J.y), cscale(QG_LD(dh, gi, n_spec, st), coeff));
+            if (d.brink) E = cadd(E, QG_LD(reinterpret_cast<const C*>(d.bh), gi, n_spec, st));
           }
           C* ep = reinterpret_cast<C*>(d.eprev);
-          const C Ep = d.ab2_first ? E : ep[gi];
-          ep[gi] = E;
+          const C Ep = d.ab2_first ? E : QG_LD(ep, gi, n_spec, st);
+          QG_ST(ep, gi, n_spec, st, E);
           const int m2 = mx * mx + my * my;
           const T k2 = T(ks2) * T(m2);
           const T ik2 = InvK2<T>::get(ks2, m2);
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           const T hdt = T(0.5) * dt;
           const T lre = -(T(d.nu) * k2 + T(d.mu));
           const T lim = beta * kx * ik2;
-          const C wz = w0[gi];
+          const C wz = QG_LD(w0, gi, n_spec, st);
           const C ab = mk<C>(T(1.5) * E.x - T(0.5) * Ep.x, T(1.5) * E.y - T(0.5) * Ep.y);
           const C num = cadd(cmul(mk<C>(T(1) + hdt * lre, hdt * lim), wz), cscale(ab, dt));
           const T dre = T(1) - hdt * lre, dim = -hdt * lim;
@@ -290,8 +295,8 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           const C wst = mk<C>((num.x * dre + num.y * dim) / den, (num.y * dre - num.x * dim) / den);
           if (d.sponge_next) {
             C* wsp = reinterpret_cast<C*>(d.wss);
-            const C wss = d.ab2_first ? wst : wsp[gi];
-            wsp[gi] = wst;
+            const C wss = d.ab2_first ? wst : QG_LD(wsp, gi, n_spec, st);
+            QG_ST(wsp, gi, n_spec, st, wst);
             wn = mk<C>(T(1.5) * wst.x - T(0.5) * wss.x, T(1.5) * wst.y - T(0.5) * wss.y);
           } else {
             wn = wst;
@@ -299,24 +304,24 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           break;
         }
         case CO_AB2CN_FINAL:
-          wn = csub(reinterpret_cast<const C*>(d.wss)[gi], slotA[e]);
+          wn = csub(QG_LD(reinterpret_cast<const C*>(d.wss), gi, n_spec, st), QG_LD(slotA, e, nspec, st));
           break;
         default:  // CO_CURL, CO_FORWARD, CO_FORWARD2
-          wn = slotA[e];
+          wn = QG_LD(slotA, e, nspec, st);
           break;
       }
-      if (d.viscous) wn = cscale(wn, vx[mx] * vy[r] * vmu);
+      if (d.viscous) wn = cscale(wn, QG_LD(vx, mx, g.Kcp, st) * QG_LD(vy, r, g.SP, st) * vmu);
       if (d.zero_mean && mx == 0 && my == 0) wn = mk<C>(T(0), T(0));
-      if (d.store_ws) reinterpret_cast<C*>(d.ws_out)[gi] = wn;
-      if (d.store_w0) w0[gi] = wn;
+      if (d.store_ws) QG_ST(reinterpret_cast<C*>(d.ws_out), gi, n_spec, st, wn);
+      if (d.store_w0) QG_ST(w0, gi, n_spec, st, wn);
       if (d.op == CO_FORWARD2) {  // the second field, treated like the first
-        C wb = slotB[e];
-        if (d.viscous) wb = cscale(wb, vx[mx] * vy[r] * vmu);
+        C wb = QG_LD(slotB, e, nspec, st);
+        if (d.viscous) wb = cscale(wb, QG_LD(vx, mx, g.Kcp, st) * QG_LD(vy, r, g.SP, st) * vmu);
         if (d.zero_mean && mx == 0 && my == 0) wb = mk<C>(T(0), T(0));
-        reinterpret_cast<C*>(d.w0b)[gi] = wb;
+        QG_ST(reinterpret_cast<C*>(d.w0b), gi, n_spec, st, wb);
       }
     }
-    slotA[e] = wn;
+    QG_ST(slotA, e, nspec, st, wn);
   }
   __syncthreads();
 
@@ -332,14 +337,14 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
       int r = -1;
       if (row <= g.K) r = row;
       else if (row >= N - g.K) r = row - N + Ny;
-      if (r >= 0 && mx < g.Kc) v = derive<T>(code, slotA[(size_t)c * Ny + r], mx, my_of_r(g, r), g, ks2, d.test_m2max, scale, U);
-      tile[e] = v;
+      if (r >= 0 && mx < g.Kc) v = derive<T>(code, QG_LD(slotA, (long long)c * Ny + r, nspec, st), mx, my_of_r(g, r), g, ks2, d.test_m2max, scale, U);
+      QG_ST(tile, e, n_tile, st, v);
     }
-    fft_batched<C>(tile, plan, W, tw, +1);
+    fft_batched<C>(tile, plan, W, tw, +1, st);
     C* dst = reinterpret_cast<C*>(d.dout[q]);
     for (int e = tid; e < N * W; e += nt) {
       const int y = e / W, c = e - y * W;
-      dst[(size_t)y * g.IP + c0 + c] = tile[e];
+      QG_ST(dst, (long long)y * g.IP + c0 + c, n_mixed, st, QG_LD(tile, e, n_tile, st));
     }
     __syncthreads();
   }
@@ -349,7 +354,7 @@ template <typename T>
 cudaError_t launch_col(const Geom& g, const FftPlan& plan, const ColDesc& d, const void* tw, int W, int threads,
                        size_t smem, cudaStream_t st) {
   auto k = col_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit<col_kernel<T>>(smem);
   if (e != cudaSuccess) return e;
   k<<<g.Kcp / W, threads, smem, st>>>(g, plan, d, reinterpret_cast<const cplx_t<T>*>(tw), W);
   return cudaGetLastError();

@@ -34,12 +34,12 @@ namespace fast {
 
 template <int N> struct RowCfg {
   static constexpr int TT = N / elems_per_thread(N);
-  static constexpr int ROWS = TT >= 128 ? 1 : 128 / TT;
+  static constexpr int ROWS = TT >= QG_ROW_CTA_THREADS ? 1 : QG_ROW_CTA_THREADS / TT;
   static constexpr int THREADS = TT * ROWS;
 };
 // resident CTAs per SM requested from the register allocator (FP32; FP64 takes 1)
 template <typename T, int OP = -1> struct Occ {
-  static constexpr int row = QG_ROW_MINB;
+  static constexpr int row = QG_ROW_MINB * 128 / QG_ROW_CTA_THREADS > 0 ? QG_ROW_MINB * 128 / QG_ROW_CTA_THREADS : 1;
   static constexpr int col = OP == CO_DYN_REDUCE ? QG_COL_MINB_REDUCE
                              : (OP == CO_FORWARD || OP == CO_FORWARD2 || OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
                              : OP == CO_CURL    ? QG_COL_MINB_CURL
@@ -374,7 +374,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
     tma::mbar_init(&mbar[1], 1);
     tma::fence_mbar_init();
     if constexpr (OP != CO_DERIVE && OP != CO_DYN_COMBINE && OP != CO_AB2CN_COMBINE) {
-      for (int f = 0; f < d.nfwd && f < NSTG; ++f) {
+      const bool stall = (int)blockIdx.x + 1 == d.stall_cta1;
+      if (stall && d.nfwd > 0) {
+        // injected stall (failure-handling test): the first tile is expected but never requested
+        tma::mbar_expect_tx(&mbar[0], FIELD_BYTES);
+      }
+      for (int f = 0; f < d.nfwd && f < NSTG && !stall; ++f) {
         tma::mbar_expect_tx(&mbar[f], FIELD_BYTES);
         for (int bx = 0; bx < NBOX; ++bx)
           tma::load_2d(reinterpret_cast<unsigned char*>(stage[f]) + (size_t)bx * BR * W * sizeof(C), &tm.in[f],
@@ -834,14 +839,8 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
 #define QG_ROW_CASE(P)                                                                                   \
   case P: {                                                                                              \
     auto k = fast::row_fast_kernel<T, N, P>;                                                            \
-    static unsigned long long attr_done = 0ull;                                                         \
-    int dev_ = 0;                                                                                        \
-    cudaGetDevice(&dev_);                                                                                \
-    if (dev_ >= 64 || !(attr_done >> dev_ & 1ull)) {                                                     \
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
-      if (e != cudaSuccess) return e;                                                                    \
-      if (dev_ < 64) attr_done |= 1ull << dev_;                                                          \
-    }                                                                                                    \
+    e = raise_smem_limit<fast::row_fast_kernel<T, N, P>>(smem);                                          \
+    if (e != cudaSuccess) return e;                                                                      \
     e = launch_pdl(d.pdl != 0, k, dim3(grid), dim3(Cfg::THREADS), smem, st, g, d, twp);                \
     if (e != cudaSuccess) return e;                                                                      \
     break;                                                                                               \
@@ -867,14 +866,8 @@ cudaError_t launch_col_one(const Geom& g, const ColDesc& d, const cplx_t<T>* twp
   using Cfg = fast::ColCfg<N>;
   auto k = fast::col_fast_kernel<T, N, P, LEAN>;
   const size_t smem = (size_t)(LEAN ? 2 : 3) * fast::col_stage_bytes<T, N>() + 1024;
-  static unsigned long long attr_done = 0ull;  // the shared-memory attribute is set once per device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 64 || !(attr_done >> dev & 1ull)) {
-    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev < 64) attr_done |= 1ull << dev;
-  }
+  const cudaError_t e = raise_smem_limit<fast::col_fast_kernel<T, N, P, LEAN>>(smem);
+  if (e != cudaSuccess) return e;
   return launch_pdl(d.pdl != 0, k, dim3(grid), dim3(Cfg::THREADS), smem, st, g, d, twp, tm);
 }
 

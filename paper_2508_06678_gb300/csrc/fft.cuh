@@ -82,7 +82,8 @@ template <typename C, int R> __device__ __forceinline__ void dft(C* v, int s) {
 }
 
 template <typename C, int R>
-__device__ void stockham_pass(C* __restrict__ d, int N, int B, int Ns, const C* __restrict__ tw, int sign) {
+__device__ void stockham_pass(C* __restrict__ d, int N, int B, int Ns, const C* __restrict__ tw, int sign,
+                              int* st) {
   constexpr int MI = MaxItems<R>::value;
   const int NR = N / R;
   const int items = NR * B;
@@ -98,11 +99,11 @@ __device__ void stockham_pass(C* __restrict__ d, int N, int B, int Ns, const C* 
       const int j = item / B;
       const int k = j % Ns;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = d[(j + r * NR) * B + b];
+      for (int r = 0; r < R; ++r) v[i][r] = QG_LD(d, (j + r * NR) * B + b, N * B, st);
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C w = __ldg(&tw[r * k * tws]);
+          C w = QG_INB(r * k * tws, N, st) ? __ldg(&tw[r * k * tws]) : mk<C>(decltype(C::x)(1), decltype(C::x)(0));
           if (sign > 0) w.y = -w.y;
           v[i][r] = cmul(v[i][r], w);
         }
@@ -116,7 +117,7 @@ __device__ void stockham_pass(C* __restrict__ d, int N, int B, int Ns, const C* 
   for (int i = 0; i < MI; ++i) {
     if (ob[i] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) d[ob[i] + r * Ns * B] = v[i][r];
+      for (int r = 0; r < R; ++r) QG_ST(d, ob[i] + r * Ns * B, N * B, st, v[i][r]);
     }
   }
   __syncthreads();
@@ -125,15 +126,15 @@ __device__ void stockham_pass(C* __restrict__ d, int N, int B, int Ns, const C* 
 // Full transform of B interleaved length-N sequences.  Synchronises on entry
 // and exit.  Requires blockDim.x * MaxItems<R> >= (N / R) * B for every pass.
 template <typename C>
-__device__ void fft_batched(C* d, const FftPlan& p, int B, const C* __restrict__ tw, int sign) {
+__device__ void fft_batched(C* d, const FftPlan& p, int B, const C* __restrict__ tw, int sign, int* st = nullptr) {
   __syncthreads();
   int Ns = 1;
   for (int s = 0; s < p.npass; ++s) {
     const int R = p.radix[s];
-    if (R == 8) stockham_pass<C, 8>(d, p.n, B, Ns, tw, sign);
-    else if (R == 4) stockham_pass<C, 4>(d, p.n, B, Ns, tw, sign);
-    else if (R == 2) stockham_pass<C, 2>(d, p.n, B, Ns, tw, sign);
-    else stockham_pass<C, 3>(d, p.n, B, Ns, tw, sign);
+    if (R == 8) stockham_pass<C, 8>(d, p.n, B, Ns, tw, sign, st);
+    else if (R == 4) stockham_pass<C, 4>(d, p.n, B, Ns, tw, sign, st);
+    else if (R == 2) stockham_pass<C, 2>(d, p.n, B, Ns, tw, sign, st);
+    else stockham_pass<C, 3>(d, p.n, B, Ns, tw, sign, st);
     Ns *= R;
   }
 }

@@ -16,7 +16,15 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <atomic>
+#include <mutex>
+#include <type_traits>
 #include <utility>
+
+// threads per CTA of the register-resident row pass (whole rows of N / 16 or N / 12 threads each)
+#ifndef QG_ROW_CTA_THREADS
+#define QG_ROW_CTA_THREADS 128
+#endif
 
 namespace qg {
 
@@ -126,6 +134,7 @@ struct RowDesc {
   const void* factor;  // RP_SCALE: physical factor field
   int check_finite;    // set *flag if a product is not finite
   int* flag;
+  int* err;            // status bits of the bounds-checked debug build (NULL: not reported)
   int pdl;             // host side: launch with programmatic stream serialisation
 };
 
@@ -178,6 +187,8 @@ struct ColDesc {
   int pdl;             // host side: launch with programmatic stream serialisation
   int* flag;           // stop flag checked at entry (NULL: always run)
   int* err;            // status bits raised by bounded waits that give up (NULL: not reported)
+  int stall_cta1;      // failure-handling test only (0 otherwise): CTA stall_cta1 - 1 arms its first tile's
+                       // mbarrier but issues no copy at all, so its bounded wait runs out with nothing in flight
 };
 
 // Per-thread accumulator of the Germano sums.  FP64 fields accumulate in
@@ -215,6 +226,61 @@ cudaError_t launch_pdl(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t 
   cfg.attrs = at;
   cfg.numAttrs = pdl && pdl_enabled() ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+// Status bit of the bounds-checked debug build (-DQG_CHECKED): some kernel met an index outside its array.
+constexpr int kFlagBounds = 4;
+
+// Index checks of the debug build.  QG_INB(i, n, st) is true when 0 <= i < n; otherwise it sets kFlagBounds in
+// *st (when st is not NULL) and is false, and the caller skips the access (a load yields zero).  In the release
+// build it is the constant true and the check compiles away.
+#ifdef QG_CHECKED
+__device__ __forceinline__ bool qg_in_bounds(long long i, long long n, int* st) {
+  if (i >= 0 && i < n) return true;
+  if (st) atomicOr(st, kFlagBounds);
+  return false;
+}
+#define QG_INB(i, n, st) ::qg::qg_in_bounds((long long)(i), (long long)(n), (st))
+#else
+#define QG_INB(i, n, st) true
+#endif
+// checked load p[i] of an array of n elements (zero when out of range in the debug build)
+template <typename E>
+__device__ __forceinline__ std::remove_cv_t<E> qg_load(E* p, long long i, long long n, int* st) {
+#ifdef QG_CHECKED
+  if (!qg_in_bounds(i, n, st)) return std::remove_cv_t<E>{};
+#else
+  (void)n;
+  (void)st;
+#endif
+  return p[i];
+}
+#define QG_LD(p, i, n, st) ::qg::qg_load((p), (long long)(i), (long long)(n), (st))
+// checked store p[i] = v
+#define QG_ST(p, i, n, st, v)              \
+  do {                                     \
+    if (QG_INB((i), (n), (st))) (p)[(i)] = (v); \
+  } while (0)
+
+// Raise kernel KERNEL's dynamic shared-memory limit on the current device to at least `bytes`.  The limit only
+// ever rises: each (kernel, device) keeps a high-water mark, raised under a lock, so one host thread can never
+// lower the limit between another thread's raise and its launch (a launch with a larger request would then fail).
+template <auto KERNEL>
+cudaError_t raise_smem_limit(size_t bytes) {
+  constexpr int kDev = 64;
+  static std::atomic<int> high[kDev];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int want = (int)bytes;
+  if (dev < 0 || dev >= kDev) return cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (want <= high[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(mu);
+  if (want <= high[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (e == cudaSuccess) high[dev].store(want, std::memory_order_release);
+  return e;
 }
 
 template <typename T> struct GermanoAcc;

@@ -44,6 +44,13 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
   const int y = blockIdx.x;
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
+  // extents for the bounds-checked debug build: shared work row, physical slots, global arrays
+  int* const st = d.err;
+  unsigned dyn_smem = 0;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+  const long long nslot_el = ((long long)dyn_smem - (long long)N * (long long)sizeof(C)) / (long long)sizeof(T);
+  const long long n_mixed = (long long)N * g.IP, n_phys = (long long)N * N;
+  (void)nslot_el; (void)n_mixed; (void)n_phys; (void)st;
 
   if (d.flag) {
     const int stop = __syncthreads_or(*reinterpret_cast<volatile int*>(d.flag) != 0);
@@ -52,40 +59,40 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
 
   // ---- inputs -> physical rows in slots
   if (d.in_phys) {
-    const T* src = reinterpret_cast<const T*>(d.phys_in) + (size_t)y * N;
-    for (int x = tid; x < N; x += nt) slots[x] = src[x];
+    const T* src = reinterpret_cast<const T*>(d.phys_in);
+    for (int x = tid; x < N; x += nt) QG_ST(slots, x, nslot_el, st, QG_LD(src, (long long)y * N + x, n_phys, st));
     if (d.phys_in2) {
-      const T* src2 = reinterpret_cast<const T*>(d.phys_in2) + (size_t)y * N;
-      for (int x = tid; x < N; x += nt) slots[N + x] = src2[x];
+      const T* src2 = reinterpret_cast<const T*>(d.phys_in2);
+      for (int x = tid; x < N; x += nt)
+        QG_ST(slots, N + x, nslot_el, st, QG_LD(src2, (long long)y * N + x, n_phys, st));
     }
   } else {
     for (int p = 0; p < d.nin; p += 2) {
-      const C* A = reinterpret_cast<const C*>(d.in[p]) + (size_t)y * g.IP;
-      const C* B = (p + 1 < d.nin) ? reinterpret_cast<const C*>(d.in[p + 1]) + (size_t)y * g.IP : nullptr;
+      const C* A = reinterpret_cast<const C*>(d.in[p]);
+      const C* B = (p + 1 < d.nin) ? reinterpret_cast<const C*>(d.in[p + 1]) : nullptr;
+      const long long row0 = (long long)y * g.IP;
       for (int k = tid; k < N; k += nt) {
         C z = mk<C>(T(0), T(0));
         if (k <= g.K) {
-          C a = A[k];
-          C b = B ? B[k] : mk<C>(T(0), T(0));
+          C a = QG_LD(A, row0 + k, n_mixed, st);
+          C b = B ? QG_LD(B, row0 + k, n_mixed, st) : mk<C>(T(0), T(0));
           if (k == 0) {
             a.y = T(0);
             b.y = T(0);
           }
           z = mk<C>(a.x - b.y, a.y + b.x);
         } else if (k >= N - g.K) {
-          const C a = A[N - k];
-          const C b = B ? B[N - k] : mk<C>(T(0), T(0));
+          const C a = QG_LD(A, row0 + N - k, n_mixed, st);
+          const C b = B ? QG_LD(B, row0 + N - k, n_mixed, st) : mk<C>(T(0), T(0));
           z = mk<C>(a.x + b.y, b.x - a.y);
         }
-        work[k] = z;
+        QG_ST(work, k, N, st, z);
       }
-      fft_batched<C>(work, plan, 1, tw, +1);
-      T* sa = slots + (size_t)p * N;
-      T* sb = slots + (size_t)(p + 1) * N;
+      fft_batched<C>(work, plan, 1, tw, +1, st);
       for (int x = tid; x < N; x += nt) {
-        const C z = work[x];
-        sa[x] = z.x;
-        if (B) sb[x] = z.y;
+        const C z = QG_LD(work, x, N, st);
+        QG_ST(slots, (long long)p * N + x, nslot_el, st, z.x);
+        if (B) QG_ST(slots, (long long)(p + 1) * N + x, nslot_el, st, z.y);
       }
       __syncthreads();
     }
@@ -94,8 +101,13 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
 
   // ---- pointwise products, in place in the slots
   int bad = 0;
-  const T* fac = d.factor ? reinterpret_cast<const T*>(d.factor) + (size_t)y * N : nullptr;
+  const T* fac = d.factor ? reinterpret_cast<const T*>(d.factor) : nullptr;
   for (int x = tid; x < N; x += nt) {
+#ifdef QG_CHECKED
+    // every slot this point's program touches lies inside the dynamic shared memory
+    const int used = d.nin > d.nout ? d.nin : d.nout;
+    if (!QG_INB((long long)(used - 1) * N + x, nslot_el, st)) continue;
+#endif
     T* s = slots + x;
 #define S(i) s[(size_t)(i) * N]
     switch (d.prog) {
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
         break;
       }
       case RP_SCALE: {
-        const T f = fac[x];
+        const T f = QG_LD(fac, (long long)y * N + x, n_phys, st);
         for (int i = 0; i < d.nin; ++i) S(i) = S(i) * f;
         break;
       }
@@ -150,11 +162,12 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
   // ---- physical rows -> forward x-transform -> mixed arrays
   if (d.out_phys) {
     __syncthreads();
-    T* dst = reinterpret_cast<T*>(d.phys_out) + (size_t)y * N;
-    for (int x = tid; x < N; x += nt) dst[x] = slots[x];
+    T* dst = reinterpret_cast<T*>(d.phys_out);
+    for (int x = tid; x < N; x += nt) QG_ST(dst, (long long)y * N + x, n_phys, st, QG_LD(slots, x, nslot_el, st));
     if (d.phys_out2) {
-      T* dst2 = reinterpret_cast<T*>(d.phys_out2) + (size_t)y * N;
-      for (int x = tid; x < N; x += nt) dst2[x] = slots[N + x];
+      T* dst2 = reinterpret_cast<T*>(d.phys_out2);
+      for (int x = tid; x < N; x += nt)
+        QG_ST(dst2, (long long)y * N + x, n_phys, st, QG_LD(slots, N + x, nslot_el, st));
     }
     return;
   }
@@ -162,27 +175,29 @@ __global__ void __launch_bounds__(512) row_kernel(Geom g, FftPlan plan, RowDesc 
   for (int p = 0; p < d.nout; p += 2) {
     __syncthreads();
     const bool two = p + 1 < d.nout;
-    const T* sa = slots + (size_t)p * N;
-    const T* sb = slots + (size_t)(p + 1) * N;
-    for (int x = tid; x < N; x += nt) work[x] = mk<C>(sa[x], two ? sb[x] : T(0));
-    fft_batched<C>(work, plan, 1, tw, -1);
-    C* A = reinterpret_cast<C*>(d.out[p]) + (size_t)y * g.IP;
-    C* B = two ? reinterpret_cast<C*>(d.out[p + 1]) + (size_t)y * g.IP : nullptr;
+    for (int x = tid; x < N; x += nt)
+      QG_ST(work, x, N, st,
+            mk<C>(QG_LD(slots, (long long)p * N + x, nslot_el, st),
+                  two ? QG_LD(slots, (long long)(p + 1) * N + x, nslot_el, st) : T(0)));
+    fft_batched<C>(work, plan, 1, tw, -1, st);
+    C* A = reinterpret_cast<C*>(d.out[p]);
+    C* B = two ? reinterpret_cast<C*>(d.out[p + 1]) : nullptr;
+    const long long row0 = (long long)y * g.IP;
     const bool dxa = (d.dx_mask >> p) & 1u;
     const bool dxb = (d.dx_mask >> (p + 1)) & 1u;
     for (int k = tid; k < g.Kcp; k += nt) {
       C a = mk<C>(T(0), T(0)), b = mk<C>(T(0), T(0));
       if (k < g.Kc) {
-        const C z = work[k];
-        const C zm = work[(N - k) % N];
+        const C z = QG_LD(work, k, N, st);
+        const C zm = QG_LD(work, (N - k) % N, N, st);
         a = mk<C>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
         b = mk<C>(T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x));
         const T kx = ks * T(k);
         if (dxa) a = cmul_ik(a, kx);
         if (dxb) b = cmul_ik(b, kx);
       }
-      A[k] = a;
-      if (two) B[k] = b;
+      QG_ST(A, row0 + k, n_mixed, st, a);
+      if (two) QG_ST(B, row0 + k, n_mixed, st, b);
     }
   }
 }
@@ -191,7 +206,7 @@ template <typename T>
 cudaError_t launch_row(const Geom& g, const FftPlan& plan, const RowDesc& d, const void* tw, int threads,
                        size_t smem, cudaStream_t st) {
   auto k = row_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit<row_kernel<T>>(smem);
   if (e != cudaSuccess) return e;
   k<<<g.n, threads, smem, st>>>(g, plan, d, reinterpret_cast<const cplx_t<T>*>(tw));
   return cudaGetLastError();
