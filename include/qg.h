@@ -49,6 +49,8 @@ extern "C" {
 #define QG_ERR_OOM (-4)       /* device allocation failed */
 #define QG_ERR_TIMEOUT (-5)   /* a bounded device wait gave up (an async copy never arrived) */
 #define QG_ERR_UNSUPPORTED (-6) /* valid request the library cannot serve on this device (e.g. shared memory) */
+#define QG_ERR_BOUNDS (-7)    /* bounds-checked debug build (-DQG_CHECKED) only: a kernel met an index outside
+                                 its array; the access was skipped and stepping stopped */
 
 /* Working precision of the device fields. */
 #define QG_FP64 0
@@ -344,9 +346,26 @@ int qg_kernel_times(qg_handle* h, int32_t* counts, double* ms, int32_t nclass);
  * streams, or different host threads) race and must be serialised by the
  * caller.  The first call on each device looks up that array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Errors: QG_ERR_ARG for n > 512 or other bad
- * arguments (nothing is enqueued), QG_ERR_CUDA. */
+ * before any stream capture.  CUDA loads a library's device code lazily by
+ * default, so that first call on a device may also load this module, which
+ * reserves the static array and other module memory and can synchronise the
+ * device: a caller that needs the no-allocation guarantee from its very first
+ * use makes one warm-up call per device at set-up time; every later call
+ * allocates nothing.  Errors: QG_ERR_ARG for n > 512 or other bad arguments
+ * (nothing is enqueued), QG_ERR_CUDA. */
 int qg_field_stats_static(const void* omega, int32_t n, double L, int32_t dtype, void* cuda_stream, double* stats);
+
+/* Measured fused multiply-add throughput of the current device in dtype
+ * (QG_FP32 or QG_FP64): a kernel of independent FMA chains, 8 CTAs of 256
+ * threads per SM, calibrated to about 50 ms and timed by CUDA events (best of
+ * three launches).  The paper has no counterpart: it gives the arithmetic
+ * peak that the FP64 form of the step (bound by FP64 arithmetic, not HBM, on
+ * this GPU) is reported against.  Synchronous; allocates one scalar.
+ *   flops_per_s: output, 2 flops per FMA;  ms: output (may be NULL), the
+ *   duration of the best launch.
+ * Changes no clock or device setting.  Errors: QG_ERR_ARG, QG_ERR_OOM,
+ * QG_ERR_CUDA. */
+int qg_probe_fma_rate(int32_t dtype, double* flops_per_s, double* ms);
 
 /* Thread-local description of the last error (never NULL). */
 const char* qg_last_error(void);

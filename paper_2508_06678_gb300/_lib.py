@@ -18,6 +18,7 @@ QG_ERR_NONFINITE = -3
 QG_ERR_OOM = -4
 QG_ERR_TIMEOUT = -5
 QG_ERR_UNSUPPORTED = -6
+QG_ERR_BOUNDS = -7
 QG_FP64 = 0
 QG_FP32 = 1
 QG_SCHEME_RK3_EXACT = 0
@@ -29,6 +30,7 @@ KERNEL_CLASSES = ("row_stage", "col_reduce", "col_stage", "row_brinkman", "col_c
 ERROR_NAMES = {
     QG_ERR_ARG: "QG_ERR_ARG", QG_ERR_CUDA: "QG_ERR_CUDA", QG_ERR_NONFINITE: "QG_ERR_NONFINITE",
     QG_ERR_OOM: "QG_ERR_OOM", QG_ERR_TIMEOUT: "QG_ERR_TIMEOUT", QG_ERR_UNSUPPORTED: "QG_ERR_UNSUPPORTED",
+    QG_ERR_BOUNDS: "QG_ERR_BOUNDS",
 }
 
 
@@ -82,6 +84,7 @@ SIGNATURES = {
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int32]),
     "qg_field_stats_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
+    "qg_probe_fma_rate": (C.c_int, [C.c_int32, DP, DP]),
     "qg_last_error": (C.c_char_p, []),
     "qg_version": (C.c_char_p, []),
 }

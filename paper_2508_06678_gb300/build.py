@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqg.so")
+# the bounds-checked debug build (every shared and global access of the generic row and column passes and their
+# FFT is checked; an index outside its array sets a status bit reported as QG_ERR_BOUNDS): tests only
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_FLAGS = ("-DQG_CHECKED",)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
 
@@ -58,5 +62,12 @@ def build(verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
     return lib
 
 
+def build_checked(verbose: bool = False) -> str:
+    return build(verbose, CHECKED_FLAGS, CHECKED_DIR)
+
+
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    if "--checked" in sys.argv:
+        print(build_checked(verbose="-v" in sys.argv))
+    else:
+        print(build(verbose="-v" in sys.argv))

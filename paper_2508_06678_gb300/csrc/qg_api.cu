@@ -233,6 +233,9 @@ struct qg_handle {
   double* dev_scalars = nullptr;  // [0..2] C per stage, [4..7] diagnostics
   int* flag = nullptr;
   int* flag_host = nullptr;
+  // failure-handling test only: QG_INJECT_TMA_STALL=<cta> at creation makes that CTA of the first step's first
+  // TMA column pass wait for a tile it never requested (one shot; 0 = off, else the CTA index + 1)
+  int inject_stall = 0;
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
   int64_t step = 0;
@@ -406,6 +409,7 @@ cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
 
 int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
+  d.err = h->flag;
   Bracket br(h, cls);
   cudaError_t e;
   if (h->fast)
@@ -525,6 +529,8 @@ int enqueue_step(qg_handle* h) {
       cr.op = CO_DYN_REDUCE;
       cr.nfwd = 6;
       for (int i = 0; i < 6; ++i) cr.fin[i] = h->Y[i];
+      cr.stall_cta1 = h->inject_stall;
+      h->inject_stall = 0;
       if ((rc = run_col(h, cr, QG_K_COL_REDUCE))) return rc;
       c.op = CO_DYN_COMBINE;
       c.nfwd = 0;
@@ -533,6 +539,8 @@ int enqueue_step(qg_handle* h) {
       c.op = CO_STAGE_STATIC;
       c.nfwd = h->nout;
       for (int i = 0; i < h->nout; ++i) c.fin[i] = h->Y[i];
+      c.stall_cta1 = h->inject_stall;
+      h->inject_stall = 0;
     }
     if (s < 2) {
       c.store_ws = 1;
@@ -1464,10 +1472,11 @@ int qg_create(const qg_grid* grid, double beta, double U, const double* mask, co
     const size_t dense = (size_t)n * fw * csz, padded = (size_t)fw * (n + n / 16 + 16 / fw) * csz;
     const size_t fast_col_smem = 3 * (((dense > padded ? dense : padded) + 1023) / 1024 * 1024) + 1024;
     const int tt = spec ? n / fast::elems_per_thread(n) : 1;
-    const int rows = tt >= 128 ? 1 : 128 / tt;  // rows per CTA of the row pass
+    const int rows = tt >= QG_ROW_CTA_THREADS ? 1 : QG_ROW_CTA_THREADS / tt;  // rows per CTA of the row pass
     const size_t fast_row_smem = (size_t)2 * rows * (n + n / 16) * csz;
     h->fast = spec && fast_col_smem <= smem_cap && fast_row_smem <= smem_cap;
     if (getenv("QG_FORCE_GENERIC")) h->fast = false;
+    if (const char* inj = getenv("QG_INJECT_TMA_STALL")) h->inject_stall = h->fast ? atoi(inj) + 1 : 0;
     if (h->fast) h->W = fw;
   }
   g.Kcp = (g.Kc + h->W - 1) / h->W * h->W;
@@ -1669,6 +1678,10 @@ int qg_step(qg_handle* h, int32_t nsteps) {
   if (!h) return fail(QG_ERR_ARG, "qg_step: NULL handle");
   if (nsteps < 0) return fail(QG_ERR_ARG, "qg_step: nsteps < 0");
   if (h->flag_pending && cudaEventQuery(h->flag_event) == cudaSuccess) h->flag_pending = false;
+  if (!h->flag_pending && (*h->flag_host & kFlagBounds))
+    return fail(QG_ERR_BOUNDS, "qg_step: a kernel met an index outside its array at an earlier step");
+  if (!h->flag_pending && (*h->flag_host & kFlagTimeout))
+    return fail(QG_ERR_TIMEOUT, "qg_step: a bounded device wait gave up at an earlier step; qg_set_state resets");
   if (!h->flag_pending && *h->flag_host)
     return fail(QG_ERR_NONFINITE, "qg_step: state became non-finite at an earlier step");
   for (int i = 0; i < nsteps; ++i) {
@@ -1701,6 +1714,7 @@ int qg_sync(qg_handle* h) {
   CK(cudaStreamSynchronize(h->stream), "qg_sync");
   h->flag_pending = false;
   f = *h->flag_host;
+  if (f & kFlagBounds) return fail(QG_ERR_BOUNDS, "qg_sync: a kernel met an index outside its array (checked build)");
   if (f & kFlagTimeout) return fail(QG_ERR_TIMEOUT, "qg_sync: a bounded device wait gave up (TMA tile never arrived)");
   if (f) return fail(QG_ERR_NONFINITE, "qg_sync: state became non-finite");
   return QG_OK;
