@@ -233,9 +233,23 @@ int qg_series_compare(const void* les, int32_t n_les_snap, const void* ff, int32
  * batched form of qg_step).  Each member is a full qg_handle on a stream of
  * its own; a step of the ensemble advances every member by one step of its
  * own scheme.  After one eager step it is replayed as one CUDA graph in which
- * the members' steps are parallel branches between a fork and a join on the
+ * the members' steps are branches between a fork and a join on the
  * ensemble's stream, so members' kernels run side by side on the GPU.  A
- * member's results are bitwise those of the same member stepped alone. */
+ * member's results are bitwise those of the same member stepped alone.
+ *
+ * Launch form, chosen by a tuner at creation: the members run in L chains
+ * (lanes) side by side, dealt longest-first by estimated cost (L = count:
+ * every member in a branch of its own), with or without programmatic
+ * dependent launch, and with the FP32 Germano reduction in its lean or
+ * register form.  None of these changes a member's arithmetic.  The tuner
+ * times a few replays of each candidate's graph, stepping the members from
+ * their initial zero states, then restores those states, the step counters
+ * and the status flags; the choice is cached per signature (grids,
+ * precisions, closures, schemes, forcings, device) for later ensembles in the
+ * process.  The environment can fix the form instead: QG_ENSEMBLE_LANES=L,
+ * QG_ENSEMBLE_PDL=0|1, QG_ENSEMBLE_LEAN=0 (lean where it makes one wave) |
+ * 1 (lean wherever it fits) | 2 (never), or QG_ENSEMBLE_TUNE=0 (no timing:
+ * all members side by side, no PDL, lean where it makes one wave). */
 typedef struct qg_ensemble qg_ensemble;
 
 typedef struct {
@@ -269,6 +283,13 @@ int qg_ensemble_step(qg_ensemble* e, int32_t nsteps);
  * member that reports it, whose index goes to *first_bad (-1 if none; may be
  * NULL). */
 int qg_ensemble_sync(qg_ensemble* e, int32_t* first_bad);
+
+/* The ensemble's launch form: form[0] = lanes (1..count), form[1] = PDL
+ * (0/1), form[2] = lean-reduction setting (0, 1, 2 as QG_ENSEMBLE_LEAN),
+ * form[3] = 0 (default or fixed by the environment), 1 (timed at creation),
+ * 2 (taken from the cache); *ms_per_step (may be NULL) = the chosen form's
+ * timed ms per ensemble step (0 when not timed). */
+int qg_ensemble_config(qg_ensemble* e, int32_t* form, double* ms_per_step);
 
 /* Destroy every member and the ensemble's own streams (NULL is ignored). */
 void qg_ensemble_destroy(qg_ensemble* e);

@@ -70,3 +70,31 @@ def test_rejects_grid_beyond_static_capacity(lib):
                                    C.c_void_p(out.data_ptr()))
     assert rc == qg.QG_ERR_ARG
     assert b"512" in lib.qg_last_error()
+
+
+def test_calls_after_warm_up_allocate_no_device_memory(lib):
+    """The property the entry point exists for: once a warm-up call per device has loaded the module, further
+    calls (every size and dtype, up to the 512^2 FP64 maximum) leave the device's free memory unchanged."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    fields = {}
+    for n in (48, 512):
+        for prec, dt in ((qg.QG_FP64, torch.float64), (qg.QG_FP32, torch.float32)):
+            fields[(n, prec)] = torch.tensor(S.init_field(n, n, k_peak=n / 8), dtype=dt, device="cuda")
+
+    def call(n, prec):
+        rc = lib.qg_field_stats_static(C.c_void_p(fields[(n, prec)].data_ptr()), n, 2 * np.pi, prec,
+                                       C.c_void_p(stream.cuda_stream), C.c_void_p(out.data_ptr()))
+        assert rc == qg.QG_OK, lib.qg_last_error()
+
+    for key in fields:  # warm-up: module load, kernel attributes
+        call(*key)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for key in fields:
+            call(*key)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)
