@@ -79,6 +79,7 @@ SIGNATURES = {
     "qg_ensemble_handle": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "qg_ensemble_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "qg_ensemble_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "qg_ensemble_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), DP]),
     "qg_ensemble_destroy": (None, [C.c_void_p]),
     "qg_step_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, DP]),
     "qg_profile": (C.c_int, [C.c_void_p, C.c_int32]),

@@ -169,6 +169,11 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
           if (f == 0) QG_ST(slotA, e, nspec, st, X);
           else QG_ST(slotB, e, nspec, st, X);
           break;
+        case CO_FORWARD_N:  // field f's band straight to its own spectral array
+          if (mx < g.Kc)
+            QG_ST(reinterpret_cast<C*>(d.fout[f]), gi, n_spec, st,
+                  (d.zero_mean && mx == 0 && my == 0) ? mk<C>(T(0), T(0)) : X);
+          break;
         default:  // CO_FORWARD
           QG_ST(slotA, e, nspec, st, X);
           break;
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(ColBound<T>::value) col_kernel(Geom g, FftPlan
     __syncthreads();
   }
 
+  if (d.op == CO_FORWARD_N) return;  // every field's band is stored
   if (d.op == CO_DYN_REDUCE) {
     // deterministic block reduction of the Germano partial sums
     double hm = acc_hm.value(), mm = acc_mm.value();

@@ -41,7 +41,8 @@ template <int N> struct RowCfg {
 template <typename T, int OP = -1> struct Occ {
   static constexpr int row = QG_ROW_MINB * 128 / QG_ROW_CTA_THREADS > 0 ? QG_ROW_MINB * 128 / QG_ROW_CTA_THREADS : 1;
   static constexpr int col = OP == CO_DYN_REDUCE ? QG_COL_MINB_REDUCE
-                             : (OP == CO_FORWARD || OP == CO_FORWARD2 || OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
+                             : (OP == CO_FORWARD || OP == CO_FORWARD2 || OP == CO_FORWARD_N ||
+                                OP == CO_AB2CN_FINAL) ? QG_COL_MINB_FWD
                              : OP == CO_CURL    ? QG_COL_MINB_CURL
                                                 : QG_COL_MINB;
 };
@@ -104,15 +105,20 @@ struct RowCtx {
   const Geom* g;
   int bad;
 
-  // inverse x-transform of the pair (A + i B) of half-spectrum rows; B may be null
-  __device__ __forceinline__ void inv_pair(C* x, const void* Av, const void* Bv) {
+  // inverse x-transform of the pair (A + i B) of half-spectrum rows; B may be null.  Columns beyond kmax are
+  // known to be zero (the test-filtered fields) and are not loaded.
+  __device__ __forceinline__ void inv_pair(C* x, const void* Av, const void* Bv, int kmax = E::K) {
     const C* A = reinterpret_cast<const C*>(Av) + (size_t)y * g->IP;
     const C* B = Bv ? reinterpret_cast<const C*>(Bv) + (size_t)y * g->IP : nullptr;
 #pragma unroll
     for (int m = 0; m < E::EL; ++m) {
       const int k = t + TT * m;
       C z = mk<C>(T(0), T(0));
-      if (k <= E::K) {
+      if (k <= E::K && k > kmax) {
+        // zero column
+      } else if (k >= N - E::K && N - k > kmax) {
+        // zero column
+      } else if (k <= E::K) {
         C a = A[k];
         C b = B ? B[k] : mk<C>(T(0), T(0));
         if (k == 0) {
@@ -172,19 +178,19 @@ struct RowCtx {
 // Q = g w_y with g = |grad w| (Leith) or |S| (Smagorinsky); NONE forms J only.
 template <typename T, int N, bool SMAG, bool NONE>
 __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, const void* const* in, T* J, T* P,
-                                               T* Q) {
+                                               T* Q, int kmax = Eng<T, N>::K) {
   using C = cplx_t<T>;
   using E = Eng<T, N>;
-  cx.inv_pair(x, in[0], in[1]);
+  cx.inv_pair(x, in[0], in[1], kmax);
 #pragma unroll
   for (int m = 0; m < E::EL; ++m) {
     J[m] = x[m].x;  // u_total
     P[m] = x[m].y;  // v
   }
-  cx.inv_pair(x, in[2], in[3]);  // (w_x, w_y)
+  cx.inv_pair(x, in[2], in[3], kmax);  // (w_x, w_y)
   if constexpr (SMAG) {
     C s[E::EL];
-    cx.inv_pair(s, in[4], in[5]);
+    cx.inv_pair(s, in[4], in[5], kmax);
 #pragma unroll
     for (int m = 0; m < E::EL; ++m) {
       T j, p, q;
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
         T Qk[E::EL];
 #pragma unroll
         for (int m = 0; m < E::EL; ++m) Qk[m] = Q[m];
-        level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q);
+        level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q, d.test_kmax > 0 ? d.test_kmax : E::K);
 #pragma unroll
         for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(Qk[m], Q[m]);
         cx.fwd_store(x, d.out[2], d.out[5], false, false);
@@ -283,6 +289,136 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
       cx.bad |= !isfinite(x[m].x) | !isfinite(x[m].y);
     }
     cx.fwd_store(x, d.out[0], d.nout > 1 ? d.out[1] : nullptr, false, false);
+  } else if constexpr (PROG == RP_ADJ_FWD) {
+    // one stage of the step recomputed for its adjoint: inverse transforms of (u_total, v), (w_x, w_y)
+    // [, (psi_xy, psi_d)], which are kept as physical fields, then J, g w_x, g w_y (Eq. 1, 9, 10, 13) forward
+    // transformed without the i k_x factor (the adjoint's spectral combine applies it)
+    const int kind = d.adj_kind;
+    T U[E::EL], V[E::EL];
+    cx.inv_pair(x, d.in[0], d.in[1]);
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) {
+      U[m] = x[m].x;
+      V[m] = x[m].y;
+      reinterpret_cast<T*>(d.pf[0])[yN + t + TT * m] = U[m];
+      reinterpret_cast<T*>(d.pf[1])[yN + t + TT * m] = V[m];
+    }
+    cx.inv_pair(x, d.in[2], d.in[3]);
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) {
+      reinterpret_cast<T*>(d.pf[2])[yN + t + TT * m] = x[m].x;
+      reinterpret_cast<T*>(d.pf[3])[yN + t + TT * m] = x[m].y;
+    }
+    T G[E::EL];
+    if (kind == 1) {
+      C sv[E::EL];
+      cx.inv_pair(sv, d.in[4], d.in[5]);
+#pragma unroll
+      for (int m = 0; m < E::EL; ++m) {
+        reinterpret_cast<T*>(d.pf[4])[yN + t + TT * m] = sv[m].x;
+        reinterpret_cast<T*>(d.pf[5])[yN + t + TT * m] = sv[m].y;
+        G[m] = sqrt(T(4) * sv[m].x * sv[m].x + sv[m].y * sv[m].y);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < E::EL; ++m) G[m] = sqrt(x[m].x * x[m].x + x[m].y * x[m].y);
+    }
+    T Q[E::EL];
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) {
+      const T wx = x[m].x, wy = x[m].y;
+      const T J = U[m] * wx + V[m] * wy;
+      Q[m] = G[m] * wy;
+      x[m] = mk<C>(J, kind == 0 ? T(0) : G[m] * wx);
+    }
+    cx.fwd_store(x, d.out[0], kind == 0 ? nullptr : d.out[1], false, false);
+    if (kind != 0) {
+#pragma unroll
+      for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(Q[m], T(0));
+      cx.fwd_store(x, d.out[2], nullptr, false, false);
+    }
+  } else if constexpr (PROG == RP_ADJ_REV) {
+    // transposed products of one stage (the linearisation of Eq. 1, 9, 10, 13): the adjoint field lam and the
+    // transposed derivatives p = -lam_x, q = -lam_y against the kept fields u_total, v, w_x, w_y [, psi_xy,
+    // psi_d]: lam w_x, lam w_y, lam u, lam v, then g p + s w_x / g, g q + s w_y / g (Leith) or g p, g q,
+    // 4 s psi_xy / g, s psi_d / g (Smagorinsky), s = p w_x + q w_y; pairs forward transformed
+    const int kind = d.adj_kind;
+    T LM[E::EL], P[E::EL];
+    cx.inv_pair(x, d.in[0], d.in[1]);  // (lam, lam_x)
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) {
+      LM[m] = x[m].x;
+      P[m] = -x[m].y;
+    }
+    cx.inv_pair(x, d.in[2], nullptr);  // lam_y
+    T Qv[E::EL];
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) Qv[m] = -x[m].x;
+    const T* fu = reinterpret_cast<const T*>(d.pf[0]) + yN;
+    const T* fv = reinterpret_cast<const T*>(d.pf[1]) + yN;
+    const T* fwx = reinterpret_cast<const T*>(d.pf[2]) + yN;
+    const T* fwy = reinterpret_cast<const T*>(d.pf[3]) + yN;
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(LM[m] * fwx[t + TT * m], LM[m] * fwy[t + TT * m]);
+    cx.fwd_store(x, d.out[0], d.out[1], false, false);
+#pragma unroll
+    for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(LM[m] * fu[t + TT * m], LM[m] * fv[t + TT * m]);
+    cx.fwd_store(x, d.out[2], d.out[3], false, false);
+    if (kind != 0) {
+      T S6[E::EL], S7[E::EL];
+#pragma unroll
+      for (int m = 0; m < E::EL; ++m) {
+        const T wx = fwx[t + TT * m], wy = fwy[t + TT * m];
+        const T s = P[m] * wx + Qv[m] * wy;
+        T g, a, b;
+        if (kind == 1) {
+          const T pxy = reinterpret_cast<const T*>(d.pf[4])[yN + t + TT * m];
+          const T pd = reinterpret_cast<const T*>(d.pf[5])[yN + t + TT * m];
+          g = sqrt(T(4) * pxy * pxy + pd * pd);
+          const T ig = g > T(0) ? T(1) / g : T(0);
+          a = g * P[m];
+          b = g * Qv[m];
+          S6[m] = T(4) * s * pxy * ig;
+          S7[m] = s * pd * ig;
+        } else {
+          g = sqrt(wx * wx + wy * wy);
+          const T ig = g > T(0) ? T(1) / g : T(0);
+          a = g * P[m] + s * wx * ig;
+          b = g * Qv[m] + s * wy * ig;
+          S6[m] = T(0);
+          S7[m] = T(0);
+        }
+        x[m] = mk<C>(a, b);
+      }
+      cx.fwd_store(x, d.out[4], d.out[5], false, false);
+      if (kind == 1) {
+#pragma unroll
+        for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(S6[m], S7[m]);
+        cx.fwd_store(x, d.out[6], d.out[7], false, false);
+      }
+    }
+  } else if (d.npair > 0) {  // RP_COPY of npair pairs in one launch (one FFT code copy, a runtime loop)
+#pragma unroll 1
+    for (int p = 0; p < d.npair; ++p) {
+      if (d.in_phys) {
+        const T* src = reinterpret_cast<const T*>(d.pin[2 * p]) + yN;
+        const T* src2 = d.pin[2 * p + 1] ? reinterpret_cast<const T*>(d.pin[2 * p + 1]) + yN : nullptr;
+#pragma unroll
+        for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(src[t + TT * m], src2 ? src2[t + TT * m] : T(0));
+        cx.fwd_store(x, d.out[2 * p], src2 ? d.out[2 * p + 1] : nullptr, false, false);
+      } else {
+        void* dst2v = d.pout[2 * p + 1];
+        cx.inv_pair(x, d.in[2 * p], dst2v ? d.in[2 * p + 1] : nullptr);
+        T* dst = reinterpret_cast<T*>(d.pout[2 * p]) + yN;
+#pragma unroll
+        for (int m = 0; m < E::EL; ++m) dst[t + TT * m] = x[m].x;
+        if (dst2v) {
+          T* dst2 = reinterpret_cast<T*>(dst2v) + yN;
+#pragma unroll
+          for (int m = 0; m < E::EL; ++m) dst2[t + TT * m] = x[m].y;
+        }
+      }
+    }
   } else {  // RP_COPY: one or two physical rows in or out (two as the real and imaginary parts of one FFT)
     if (d.in_phys) {
       const T* src = reinterpret_cast<const T*>(d.phys_in) + yN;
@@ -550,6 +686,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
         } else if constexpr (OP == CO_FORWARD2) {
           if (f == 0) A[m] = X;
           else B[m] = X;
+        } else if constexpr (OP == CO_FORWARD_N) {
+          const bool kept = (k <= K || k >= N - K) && col_ok;
+          if (kept) {
+            const C v = (d.zero_mean && mx == 0 && my == 0) ? mk<C>(T(0), T(0)) : X;
+            reinterpret_cast<C*>(d.fout[f])[colbase + (k <= K ? k : k - N + Ny)] = v;
+          }
         } else {  // CO_FORWARD, CO_AB2CN_FINAL
           A[m] = X;
         }
@@ -557,7 +699,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
     }
   }
 
-  if constexpr (OP == CO_DYN_REDUCE) {
+  if constexpr (OP == CO_FORWARD_N) {
+    return;  // every field's band is stored; no state update, no derived fields, no bulk stores in flight
+  } else if constexpr (OP == CO_DYN_REDUCE) {
     double hm = acc_hm.value(), mm = acc_mm.value();
     for (int o = 16; o > 0; o >>= 1) {
       hm += __shfl_down_sync(0xffffffffu, hm, o);
@@ -853,6 +997,8 @@ cudaError_t launch_row_fast(const Geom& g, const RowDesc& d, const void* tw, cud
     QG_ROW_CASE(RP_DSMAG)
     QG_ROW_CASE(RP_SCALE)
     QG_ROW_CASE(RP_COPY)
+    QG_ROW_CASE(RP_ADJ_FWD)
+    QG_ROW_CASE(RP_ADJ_REV)
     default:
       return cudaErrorInvalidValue;
   }
@@ -900,13 +1046,16 @@ cudaError_t launch_col_fast(const Geom& g, const ColDesc& d, const void* tw, con
     QG_COL_CASE(CO_CURL)
     QG_COL_CASE(CO_FORWARD)
     QG_COL_CASE(CO_FORWARD2)
+    QG_COL_CASE(CO_FORWARD_N)
     QG_COL_CASE(CO_AB2CN)
     QG_COL_CASE(CO_AB2CN_COMBINE)
     QG_COL_CASE(CO_AB2CN_FINAL)
     case CO_DYN_REDUCE:
       if constexpr (fast::lean_fits<T, N>()) {
-        // the lean form when the columns need more than one wave at two CTAs per SM but one at three
-        if (d.scr[0] && d.scr[1] && d.scr[2] && grid > 2 * device_sms() && grid <= 3 * device_sms())
+        // the lean form when the columns need more than one wave at two CTAs per SM but one at three (or
+        // whenever the caller asks for it)
+        const bool one_wave = grid > 2 * device_sms() && grid <= 3 * device_sms();
+        if (d.scr[0] && d.scr[1] && d.scr[2] && (d.lean == 1 || (d.lean == 0 && one_wave)))
           return launch_col_one<T, N, CO_DYN_REDUCE, true>(g, d, twp, tm, grid, st);
       }
       return launch_col_one<T, N, CO_DYN_REDUCE, false>(g, d, twp, tm, grid, st);

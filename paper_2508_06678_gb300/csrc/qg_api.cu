@@ -25,6 +25,10 @@
 #include <string>
 #include <array>
 #include <utility>
+#include <algorithm>
+#include <limits>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -236,6 +240,10 @@ struct qg_handle {
   // failure-handling test only: QG_INJECT_TMA_STALL=<cta> at creation makes that CTA of the first step's first
   // TMA column pass wait for a tile it never requested (one shot; 0 = off, else the CTA index + 1)
   int inject_stall = 0;
+  // launch forms of the step chosen by an ensemble's tuner: programmatic dependent launch, the FP32 Germano
+  // reduction's lean form (ColDesc::lean); both leave the arithmetic unchanged
+  int step_pdl = 0;
+  int lean_reduce = 0;
   cudaEvent_t flag_event = nullptr;
   bool flag_pending = false;
   int64_t step = 0;
@@ -410,6 +418,7 @@ cudaError_t col_fast_dispatch(qg_handle* h, const ColDesc& d) {
 int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
   d.err = h->flag;
+  if (h->step_pdl) d.pdl = 1;
   Bracket br(h, cls);
   cudaError_t e;
   if (h->fast)
@@ -425,6 +434,8 @@ int run_row(qg_handle* h, RowDesc& d, int cls, bool use_flag = true) {
 int run_col(qg_handle* h, ColDesc& d, int cls, bool use_flag = true) {
   d.flag = use_flag ? h->flag : nullptr;
   d.err = h->flag;
+  if (h->step_pdl) d.pdl = 1;
+  d.lean = h->lean_reduce;
   Bracket br(h, cls);
   cudaError_t e;
   if (h->fast)
@@ -513,6 +524,7 @@ int enqueue_step(qg_handle* h) {
     r.nin = h->nin;
     r.nout = h->nout;
     r.dx_mask = h->dx_mask;
+    r.test_kmax = h->test_kmax;
     r.check_finite = 1;
     for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
     for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
@@ -644,6 +656,7 @@ int enqueue_step_ab2(qg_handle* h) {
   r.nin = h->nin;
   r.nout = h->nout;
   r.dx_mask = h->dx_mask;
+  r.test_kmax = h->test_kmax;
   r.check_finite = 1;
   for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
   for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
@@ -728,7 +741,7 @@ int enqueue_any_step(qg_handle* h) { return h->scheme == QG_SCHEME_AB2CN ? enque
 // ---------------------------------------------------------------------------
 constexpr int kAdjNS = 25;  // spectral: w0..w3, w5, lam, lam', acc, 11 product spectra, 3 x 2 stage SGS fluxes
 constexpr int kAdjNP = 37;  // physical: 6 fields, 3 adjoint fields, 8 products, input, output, 3 x 6 stage fields
-constexpr int kAdjNM = 6;   // mixed: the outputs of one derive pass
+constexpr int kAdjNM = 8;   // mixed: the outputs of one derive pass, or one batch of forward transforms
 constexpr int kAdjStageP = 19;  // first of the per-stage physical fields (u, v, w_x, w_y, psi_xy, psi_d)
 constexpr int kAdjStageS = 19;  // first of the per-stage spectral SGS fluxes F[g w_x], F[g w_y]
 // dynamic closures only: per stage the test-level state G w, H and M (spectral), G w's fields (physical),
@@ -791,39 +804,55 @@ int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   return run_col(h, c, QG_K_ADJ_COL, false);
 }
 
-// spectral bands of several physical fields: row passes take them in pairs (one complex FFT per pair)
+// spectral bands of several physical fields (at most kAdjNM): the row passes take them in pairs (one complex FFT
+// per pair; the register-resident kernels take every pair in one launch), then one column pass transforms them
+// all, each to its own spectral array
 int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::initializer_list<void*> S) {
   std::vector<const void*> p(P);
   std::vector<void*> s(S);
+  const int n = (int)p.size();
+  if (n < 1 || n > kAdjNM || (int)s.size() != n) return fail(QG_ERR_ARG, "adjoint: bad transform batch");
   int rc = QG_OK;
-  for (size_t i = 0; i < p.size() && !rc; i += 2) {
-    const bool two = i + 1 < p.size();
+  if (h->fast && n > 2) {
     RowDesc r{};
-  r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
+    r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
     r.prog = RP_COPY;
     r.nin = 1;
-    r.nout = two ? 2 : 1;
+    r.nout = n;
     r.in_phys = 1;
-    r.phys_in = p[i];
-    r.phys_in2 = two ? p[i + 1] : nullptr;
-    r.out[0] = h->adj_M[0];
-    r.out[1] = h->adj_M[1];
+    r.npair = (n + 1) / 2;
+    for (int i = 0; i < n; ++i) {
+      r.pin[i] = p[i];
+      r.out[i] = h->adj_M[i];
+    }
     rc = run_row(h, r, QG_K_ADJ_ROW, false);
-    if (rc) break;
-    // one column pass per pair: the first field to s[i], the second to s[i + 1]
-    ColDesc c = col_base(h);
-    c.pdl = 1;
-    c.op = two ? CO_FORWARD2 : CO_FORWARD;
-    c.nfwd = two ? 2 : 1;
-    c.fin[0] = h->adj_M[0];
-    c.fin[1] = two ? h->adj_M[1] : nullptr;
-    c.w0 = s[i];
-    c.w0b = two ? s[i + 1] : nullptr;
-    c.store_w0 = 1;
-    c.nder = 0;
-    rc = run_col(h, c, QG_K_ADJ_COL, false);
+  } else {
+    for (int i = 0; i < n && !rc; i += 2) {
+      const bool two = i + 1 < n;
+      RowDesc r{};
+      r.pdl = 1;
+      r.prog = RP_COPY;
+      r.nin = 1;
+      r.nout = two ? 2 : 1;
+      r.in_phys = 1;
+      r.phys_in = p[i];
+      r.phys_in2 = two ? p[i + 1] : nullptr;
+      r.out[0] = h->adj_M[i];
+      r.out[1] = two ? h->adj_M[i + 1] : nullptr;
+      rc = run_row(h, r, QG_K_ADJ_ROW, false);
+    }
   }
-  return rc;
+  if (rc) return rc;
+  ColDesc c = col_base(h);
+  c.pdl = 1;
+  c.op = CO_FORWARD_N;
+  c.nfwd = n;
+  for (int i = 0; i < n; ++i) {
+    c.fin[i] = h->adj_M[i];
+    c.fout[i] = s[i];
+  }
+  c.nder = 0;
+  return run_col(h, c, QG_K_ADJ_COL, false);
 }
 
 // physical fields of derived spectra (codes D_W, D_U (with U), D_V, D_WX, D_WY, D_PXY, D_PD) of a spectral
@@ -841,10 +870,25 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
   }
   int rc = run_col(h, c, QG_K_ADJ_COL, false);
   std::vector<void*> dst(P);
+  if (!rc && h->fast && dst.size() > 2) {
+    // every pair in one launch of the register-resident row pass
+    RowDesc r{};
+    r.pdl = 1;
+    r.prog = RP_COPY;
+    r.nin = (int)dst.size();
+    r.nout = 1;
+    r.out_phys = 1;
+    r.npair = (int)(dst.size() + 1) / 2;
+    for (size_t i = 0; i < dst.size(); ++i) {
+      r.in[i] = h->adj_M[i];
+      r.pout[i] = dst[i];
+    }
+    return run_row(h, r, QG_K_ADJ_ROW, false);
+  }
   for (size_t i = 0; i < dst.size() && !rc; i += 2) {
     const bool two = i + 1 < dst.size();
     RowDesc r{};
-  r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
+    r.pdl = 1;  // the adjoint's chains of small launches overlap their launch latency
     r.prog = RP_COPY;
     r.nin = two ? 2 : 1;
     r.nout = 1;
@@ -949,6 +993,94 @@ int adj_scalar_op(qg_handle* h, int op, const double* x0, const double* x1, cons
   return QG_OK;
 }
 
+// Fused forms of the register-resident kernels.  Forward: the stage fields of Sw (one derive pass), one row pass
+// that keeps them as physical fields P[f0..] and forms J, g w_x, g w_y in registers, one column pass to the
+// spectral arrays o0 [, o1, o2].  Reverse: lam = D_W of Sl and the derivatives D_WX, D_WY of Sd (derive passes),
+// one row pass of the transposed products against the fields at P[f0..], one column pass to S[8..].
+int adj_fused_fwd(qg_handle* h, int kind, const void* Sw, int f0, void* o0, void* o1, void* o2) {
+  auto& P = h->adj_P;
+  auto& M = h->adj_M;
+  static const int codes[6] = {D_U, D_V, D_WX, D_WY, D_PXY, D_PD};
+  const int nf = kind == AK_SMAG ? 6 : 4;
+  const int no = kind == AK_NONE ? 1 : 3;
+  ColDesc c = col_base(h);
+  c.pdl = 1;
+  c.op = CO_DERIVE;
+  c.w0 = const_cast<void*>(Sw);
+  c.nder = nf;
+  for (int i = 0; i < nf; ++i) {
+    c.der[i] = codes[i];
+    c.dout[i] = M[i];
+  }
+  int rc = run_col(h, c, QG_K_ADJ_COL, false);
+  if (rc) return rc;
+  RowDesc r{};
+  r.pdl = 1;
+  r.prog = RP_ADJ_FWD;
+  r.adj_kind = kind;
+  r.nin = nf;
+  r.nout = no;
+  for (int i = 0; i < nf; ++i) {
+    r.in[i] = M[i];
+    r.pf[i] = P[f0 + i];
+  }
+  for (int i = 0; i < no; ++i) r.out[i] = M[i];  // each row is read in full before it is written
+  rc = run_row(h, r, QG_K_ADJ_ROW, false);
+  if (rc) return rc;
+  ColDesc f = col_base(h);
+  f.pdl = 1;
+  f.op = CO_FORWARD_N;
+  f.nfwd = no;
+  void* outs[3] = {o0, o1, o2};
+  for (int i = 0; i < no; ++i) {
+    f.fin[i] = M[i];
+    f.fout[i] = outs[i];
+  }
+  return run_col(h, f, QG_K_ADJ_COL, false);
+}
+
+int adj_derive(qg_handle* h, const void* S, std::initializer_list<int> codes, int m0) {
+  ColDesc c = col_base(h);
+  c.pdl = 1;
+  c.op = CO_DERIVE;
+  c.w0 = const_cast<void*>(S);
+  c.nder = 0;
+  for (int code : codes) {
+    c.der[c.nder] = code;
+    c.dout[c.nder] = h->adj_M[m0 + c.nder];
+    ++c.nder;
+  }
+  return run_col(h, c, QG_K_ADJ_COL, false);
+}
+
+// the row and column passes of the fused reverse products once adj_M[0..2] hold lam, lam_x, lam_y
+int adj_fused_rev_tail(qg_handle* h, int kind, int f0) {
+  auto& P = h->adj_P;
+  auto& M = h->adj_M;
+  auto& S = h->adj_S;
+  const int no = kind == AK_SMAG ? 8 : kind == AK_LEITH ? 6 : 4;
+  RowDesc r{};
+  r.pdl = 1;
+  r.prog = RP_ADJ_REV;
+  r.adj_kind = kind;
+  r.nin = 3;
+  r.nout = no;
+  for (int i = 0; i < 3; ++i) r.in[i] = M[i];
+  for (int i = 0; i < 6; ++i) r.pf[i] = P[f0 + i];
+  for (int i = 0; i < no; ++i) r.out[i] = M[i];  // lam, lam_x, lam_y of a row are read before any output row
+  int rc = run_row(h, r, QG_K_ADJ_ROW, false);
+  if (rc) return rc;
+  ColDesc f = col_base(h);
+  f.pdl = 1;
+  f.op = CO_FORWARD_N;
+  f.nfwd = no;
+  for (int i = 0; i < no; ++i) {
+    f.fin[i] = M[i];
+    f.fout[i] = S[8 + i];
+  }
+  return run_col(h, f, QG_K_ADJ_COL, false);
+}
+
 // The dynamic coefficient of stage s (Eq. 11, 12, 14; R8) from its state Sw, recomputed with the stage:
 // G w, its fields, H = J(G w) - G J(w), M = r^p D(G w) - G D(w), <HM>, <MM>, C = max(0, <HM>/<MM>).
 // SJ holds J(w); the stage's SGS flux spectra hold F[g w_x], F[g w_y].
@@ -967,9 +1099,13 @@ int adj_forward_germano(qg_handle* h, int kind, const void* Sw, const void* SJ, 
   const double rp = std::pow(h->cl.test_ratio, kind == AK_SMAG ? 2 : 3);
   const double n4 = std::pow(double(h->g.n), 4);
   int rc = adj_combine(h, Swt, false, false, {{Sw, AM_ONE | AM_TESTF, 1.0}});
-  if (!rc) rc = adj_stage_fields(h, Swt, kind, f0);
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
-  if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11]}, {T0, T1, T2});
+  if (h->fast) {
+    if (!rc) rc = adj_fused_fwd(h, kind, Swt, f0, T0, T1, T2);
+  } else {
+    if (!rc) rc = adj_stage_fields(h, Swt, kind, f0);
+    if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
+    if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11]}, {T0, T1, T2});
+  }
   if (!rc) rc = adj_combine(h, SH, false, false, {{T0, AM_ONE, 1.0}, {SJ, AM_ONE | AM_TESTF, -1.0}});
   if (!rc)
     rc = adj_combine(h, SM, false, false,
@@ -988,10 +1124,15 @@ int adj_forward_stage(qg_handle* h, int kind, bool dyn, double C, const void* S0
   const int f0 = kAdjStageP + 6 * s;
   void* Sgx = S[kAdjStageS + 2 * s];
   void* Sgy = S[kAdjStageS + 2 * s + 1];
-  int rc = adj_stage_fields(h, Sw, kind, f0);
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
-  if (!rc) rc = kind == AK_NONE ? adj_to_spec_many(h, {P[9]}, {S[8]})
-                                 : adj_to_spec_many(h, {P[9], P[10], P[11]}, {S[8], Sgx, Sgy});
+  int rc = QG_OK;
+  if (h->fast) {
+    rc = adj_fused_fwd(h, kind, Sw, f0, S[8], Sgx, Sgy);
+  } else {
+    rc = adj_stage_fields(h, Sw, kind, f0);
+    if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_FORWARD, f0));
+    if (!rc) rc = kind == AK_NONE ? adj_to_spec_many(h, {P[9]}, {S[8]})
+                                   : adj_to_spec_many(h, {P[9], P[10], P[11]}, {S[8], Sgx, Sgy});
+  }
   if (!rc && dyn) rc = adj_forward_germano(h, kind, Sw, S[8], s);
   if (rc) return rc;
   if (kind == AK_NONE)
@@ -1020,21 +1161,38 @@ int adj_reverse_germano(qg_handle* h, int kind, void* Slam_out, int s) {
   int rc = adj_scalar_op(h, AS_KAPPA, C, adj_scalar(h, s, 1), h->adj_dots + kAdjDotBlocks + s, kappa);
   if (!rc) rc = adj_combine(h, Snu, false, false, {{SH, AM_ONE, 1.0}, {SM, AM_ONE, -2.0, C}});
   // outer group, at the test-level state, filtered afterwards: mu = M, derivatives of nu
-  if (!rc) rc = adj_to_phys(h, SM, {D_W}, {P[mu]});
-  if (!rc) rc = adj_to_phys(h, Snu, {D_WX, D_WY}, {P[7], P[8]});
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjDynP + 6 * s, mu));
+  if (h->fast) {
+    if (!rc) rc = adj_derive(h, SM, {D_W}, 0);
+    if (!rc) rc = adj_derive(h, Snu, {D_WX, D_WY}, 1);
+  } else {
+    if (!rc) rc = adj_to_phys(h, SM, {D_W}, {P[mu]});
+    if (!rc) rc = adj_to_phys(h, Snu, {D_WX, D_WY}, {P[7], P[8]});
+    if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjDynP + 6 * s, mu));
+  }
   for (int pass = 0; pass < 2 && !rc; ++pass) {
     if (pass == 1) {
       // inner group, at the stage state: mu = G M, derivatives of G nu
       rc = adj_combine(h, Sg, false, false, {{SM, AM_ONE | AM_TESTF, 1.0}});
-      if (!rc) rc = adj_to_phys(h, Sg, {D_W}, {P[mu]});
+      if (h->fast) {
+        if (!rc) rc = adj_derive(h, Sg, {D_W}, 0);
+      } else {
+        if (!rc) rc = adj_to_phys(h, Sg, {D_W}, {P[mu]});
+      }
       if (!rc) rc = adj_combine(h, Sg, false, false, {{Snu, AM_ONE | AM_TESTF, 1.0}});
-      if (!rc) rc = adj_to_phys(h, Sg, {D_WX, D_WY}, {P[7], P[8]});
-      if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjStageP + 6 * s, mu));
+      if (h->fast) {
+        if (!rc) rc = adj_derive(h, Sg, {D_WX, D_WY}, 1);
+      } else {
+        if (!rc) rc = adj_to_phys(h, Sg, {D_WX, D_WY}, {P[7], P[8]});
+        if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, kAdjStageP + 6 * s, mu));
+      }
     }
-    if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12]}, {S[8], S[9], S[10], S[11]});
-    if (!rc) rc = adj_to_spec_many(h, {P[13], P[14]}, {S[12], S[13]});
-    if (!rc && kind == AK_SMAG) rc = adj_to_spec_many(h, {P[15], P[16]}, {S[14], S[15]});
+    if (!rc && h->fast)
+      rc = adj_fused_rev_tail(h, kind, pass == 0 ? kAdjDynP + 6 * s : kAdjStageP + 6 * s);
+    else if (!rc && kind == AK_SMAG)
+      rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12], P[13], P[14], P[15], P[16]},
+                            {S[8], S[9], S[10], S[11], S[12], S[13], S[14], S[15]});
+    else if (!rc)
+      rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12], P[13], P[14]}, {S[8], S[9], S[10], S[11], S[12], S[13]});
     if (rc) return rc;
     const int f = pass == 0 ? AM_TESTF : 0;
     const double sj = pass == 0 ? 1.0 : -1.0, sd = pass == 0 ? rp : -1.0;
@@ -1070,11 +1228,23 @@ int adj_reverse_stage(qg_handle* h, int kind, bool dyn, double C, const void* Sl
   auto& P = h->adj_P;
   const double dt = h->par.dt, bd = b * dt;
   const int f0 = kAdjStageP + 6 * slot;  // the stage's fields, kept by the forward recomputation
-  int rc = adj_to_phys(h, Slam, {D_W, D_WX, D_WY}, {P[6], P[7], P[8]});
-  if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, f0));
-  if (!rc) rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12]}, {S[8], S[9], S[10], S[11]});
-  if (!rc && kind != AK_NONE) rc = adj_to_spec_many(h, {P[13], P[14]}, {S[12], S[13]});
-  if (!rc && kind == AK_SMAG) rc = adj_to_spec_many(h, {P[15], P[16]}, {S[14], S[15]});
+  int rc = QG_OK;
+  if (h->fast) {
+    rc = adj_derive(h, Slam, {D_W, D_WX, D_WY}, 0);
+    if (!rc) rc = adj_fused_rev_tail(h, kind, f0);
+  } else {
+    rc = adj_to_phys(h, Slam, {D_W, D_WX, D_WY}, {P[6], P[7], P[8]});
+    if (!rc) rc = adj_products(h, adj_prod_desc(h, kind, AP_ADJOINT, f0));
+  }
+  if (!rc && h->fast) {
+    // the fused passes wrote S[8..]
+  } else if (!rc && kind == AK_SMAG)
+    rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12], P[13], P[14], P[15], P[16]},
+                          {S[8], S[9], S[10], S[11], S[12], S[13], S[14], S[15]});
+  else if (!rc && kind != AK_NONE)
+    rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12], P[13], P[14]}, {S[8], S[9], S[10], S[11], S[12], S[13]});
+  else if (!rc)
+    rc = adj_to_spec_many(h, {P[9], P[10], P[11], P[12]}, {S[8], S[9], S[10], S[11]});
   if (rc) return rc;
   AdjCombine a{};
   a.out = Slam_out;
@@ -1265,6 +1435,14 @@ struct qg_ensemble {
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
   int64_t eager_steps = 0;
+  // launch form of an ensemble step (chosen by the tuner at creation): members run in `lanes` chains (0: one
+  // per member, all side by side), filled longest-first by estimated cost; programmatic dependent launch on or
+  // off; the FP32 Germano reduction's lean form (ColDesc::lean).  None of them changes a member's arithmetic.
+  int lanes = 0, pdl = 0, lean = 0;
+  int tuned = 0;          // 0 default or forced by the environment, 1 timed at creation, 2 from the cache
+  double tuned_ms = 0.0;  // the chosen form's time per ensemble step when timed
+  std::vector<double> cost;  // estimated work per member step
+  std::vector<int> order;    // members by decreasing cost
   ~qg_ensemble() {
     if (main) cudaStreamSynchronize(main);
     if (exec) cudaGraphExecDestroy(exec);
@@ -1279,16 +1457,28 @@ struct qg_ensemble {
 
 namespace {
 
-// fork on the ensemble stream, one step of every member on its stream, join
+// fork on the ensemble stream, one step of every member on its stream, join.  Members are dealt to the lanes
+// longest-first, each to the lane with the least work so far; a member waits for the one before it in its lane.
 int ens_enqueue(qg_ensemble* e) {
   CK(cudaEventRecord(e->fork, e->main), "ensemble: fork");
-  for (size_t i = 0; i < e->h.size(); ++i) {
-    CK(cudaStreamWaitEvent(e->st[i], e->fork, 0), "ensemble: fork wait");
+  const int m = (int)e->h.size();
+  const int nl = e->lanes > 0 && e->lanes < m ? e->lanes : m;
+  std::vector<int> tail(nl, -1);
+  std::vector<double> load(nl, 0.0);
+  for (int k = 0; k < m; ++k) {
+    const int i = e->order.empty() ? k : e->order[k];
+    int l = 0;
+    for (int j = 1; j < nl; ++j)
+      if (load[j] < load[l]) l = j;
+    load[l] += e->cost.empty() ? 1.0 : e->cost[i];
+    CK(cudaStreamWaitEvent(e->st[i], tail[l] < 0 ? e->fork : e->ev[tail[l]], 0), "ensemble: fork wait");
     const int rc = enqueue_any_step(e->h[i]);
     if (rc) return rc;
     CK(cudaEventRecord(e->ev[i], e->st[i]), "ensemble: join");
-    CK(cudaStreamWaitEvent(e->main, e->ev[i], 0), "ensemble: join wait");
+    tail[l] = i;
   }
+  for (int l = 0; l < nl; ++l)
+    if (tail[l] >= 0) CK(cudaStreamWaitEvent(e->main, e->ev[tail[l]], 0), "ensemble: join wait");
   return QG_OK;
 }
 
@@ -1331,6 +1521,148 @@ void ens_build_graph(qg_ensemble* e) {
   if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) e->exec = ex;
   cudaGraphDestroy(g);
   cudaGetLastError();
+}
+
+// ---- the ensemble's tuner: the launch form of an ensemble step is chosen once per signature (the members'
+// grids, precisions, closures, schemes and forcings, in order, on one device) by timing replays of each
+// candidate's graph, and cached for later ensembles of the same signature in this process.
+struct EnsChoice {
+  int lanes, pdl, lean;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, EnsChoice> g_tune_cache;
+
+std::string ens_signature(const qg_ensemble* e) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string sig = "dev" + std::to_string(dev);
+  for (const qg_handle* x : e->h) {
+    char b[96];
+    snprintf(b, sizeof(b), "|%d:%d:%d:%d:%d:%d", x->g.n, x->fp32, x->cl.kind, x->scheme, x->fac_b ? 1 : 0,
+             x->fac_s ? 1 : 0);
+    sig += b;
+  }
+  return sig;
+}
+
+void ens_apply(qg_ensemble* e, int lanes, int pdl, int lean) {
+  e->lanes = lanes;
+  e->pdl = pdl;
+  e->lean = lean;
+  for (qg_handle* x : e->h) {
+    x->step_pdl = pdl;
+    x->lean_reduce = lean;
+  }
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  e->exec = nullptr;
+  e->graph_tried = false;
+}
+
+// one ensemble step in the current launch form, replayed `reps` times after one warm replay: ms per step, or
+// +inf when the graph cannot be built
+double ens_time_form(qg_ensemble* e, cudaEvent_t a, cudaEvent_t b, int reps) {
+  ens_build_graph(e);
+  if (!e->exec) return std::numeric_limits<double>::infinity();
+  if (cudaGraphLaunch(e->exec, e->main) != cudaSuccess) return std::numeric_limits<double>::infinity();
+  cudaEventRecord(a, e->main);
+  for (int r = 0; r < reps; ++r) cudaGraphLaunch(e->exec, e->main);
+  cudaEventRecord(b, e->main);
+  float ms = 0.f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return std::numeric_limits<double>::infinity();
+  }
+  return ms / reps;
+}
+
+// Choose the launch form.  The environment can fix it (QG_ENSEMBLE_LANES, QG_ENSEMBLE_PDL, QG_ENSEMBLE_LEAN) or
+// turn the timing off (QG_ENSEMBLE_TUNE=0: all members side by side, no PDL, automatic lean form).  Timing steps
+// the members from their initial (zero) states; afterwards the states, step counters, histories and status flags
+// are reset, so the ensemble starts exactly as an untuned one.
+int ens_tune(qg_ensemble* e) {
+  const int m = (int)e->h.size();
+  e->cost.resize(m);
+  for (int i = 0; i < m; ++i) {
+    const qg_handle* x = e->h[i];
+    const double n2 = (double)x->g.n * x->g.n;
+    const double per = x->dynamic ? 2.0 : 1.0;  // the dynamic closures double the transforms
+    e->cost[i] = per * n2 * std::log2(n2) * (x->fp32 ? 1.0 : 8.0);
+  }
+  e->order.resize(m);
+  for (int i = 0; i < m; ++i) e->order[i] = i;
+  std::stable_sort(e->order.begin(), e->order.end(), [&](int a, int b) { return e->cost[a] > e->cost[b]; });
+  const char* fl = getenv("QG_ENSEMBLE_LANES");
+  const char* fp = getenv("QG_ENSEMBLE_PDL");
+  const char* fn = getenv("QG_ENSEMBLE_LEAN");
+  const char* ft = getenv("QG_ENSEMBLE_TUNE");
+  if (fl || fp || fn || (ft && atoi(ft) == 0) || getenv("QG_NO_GRAPH")) {
+    ens_apply(e, fl ? std::max(0, atoi(fl)) : 0, fp ? (atoi(fp) != 0) : 0, fn ? std::max(0, std::min(2, atoi(fn))) : 0);
+    return QG_OK;
+  }
+  const std::string sig = ens_signature(e);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      ens_apply(e, it->second.lanes, it->second.pdl, it->second.lean);
+      e->tuned = 2;
+      e->tuned_ms = it->second.ms;
+      return QG_OK;
+    }
+  }
+  // one eager step (kernel attributes, the AB2CN Euler start), then the candidates' graphs
+  int rc = ens_enqueue(e);
+  if (rc) return rc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a), "ensemble tuner: event");
+  CK(cudaEventCreate(&b), "ensemble tuner: event");
+  const int reps = 3;
+  EnsChoice best{0, 0, 0, std::numeric_limits<double>::infinity()};
+  auto trial = [&](int lanes, int pdl, int lean) {
+    ens_apply(e, lanes, pdl, lean);
+    const double t = ens_time_form(e, a, b, reps);
+    if (t < best.ms) best = {lanes, pdl, lean, t};
+  };
+  // lanes first (all side by side, then fewer chains), then PDL, then the lean reduction
+  std::vector<int> lane_set = {0};
+  for (int l : {48, 32, 24, 16, 12, 8, 6, 4, 2})
+    if (l < m) lane_set.push_back(l);
+  for (int l : lane_set) trial(l, 0, 0);
+  trial(best.lanes, 1, best.lean);
+  bool lean_possible = false;
+  for (const qg_handle* x : e->h) lean_possible = lean_possible || (x->fast && x->fp32 && x->dynamic);
+  if (lean_possible) trial(best.lanes, best.pdl, 1);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!(best.ms < std::numeric_limits<double>::infinity())) best = {0, 0, 0, 0.0};
+  ens_apply(e, best.lanes, best.pdl, best.lean);
+  e->tuned = 1;
+  e->tuned_ms = best.ms;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[sig] = best;
+  }
+  // back to the initial state: zero states and stage fields (what a step reads first), counters, histories
+  // and flags
+  for (qg_handle* x : e->h) {
+    const size_t spec_bytes = (size_t)x->g.Kcp * x->g.SP * 2 * x->esz;
+    const size_t mixed_bytes = (size_t)x->g.n * x->g.IP * 2 * x->esz;
+    CK(cudaMemsetAsync(x->w0, 0, spec_bytes, x->stream), "ensemble tuner: reset");
+    for (int i = 0; i < kMaxIn; ++i)
+      if (x->X[i]) CK(cudaMemsetAsync(x->X[i], 0, mixed_bytes, x->stream), "ensemble tuner: reset");
+    CK(cudaMemsetAsync(x->flag, 0, sizeof(int), x->stream), "ensemble tuner: reset");
+    CK(cudaStreamSynchronize(x->stream), "ensemble tuner: reset");
+    *x->flag_host = 0;
+    x->flag_pending = false;
+    x->step = 0;
+    x->t = 0.0;
+    x->ab2_hist = false;
+    memset(x->launches, 0, sizeof(x->launches));
+  }
+  CK(cudaStreamSynchronize(e->main), "ensemble tuner: sync");
+  e->eager_steps = 1;
+  return QG_OK;
 }
 
 }  // namespace
@@ -1825,7 +2157,23 @@ int qg_ensemble_create(const qg_member* members, int32_t count, void* cuda_strea
     }
     e->h.push_back(x);
   }
+  const int rc = ens_tune(e);
+  if (rc != QG_OK) {
+    const std::string why = g_err;
+    delete e;
+    return fail(rc, "qg_ensemble_create: tuning: %s", why.c_str());
+  }
   *out = e;
+  return QG_OK;
+}
+
+int qg_ensemble_config(qg_ensemble* e, int32_t* form, double* ms_per_step) {
+  if (!e || !form) return fail(QG_ERR_ARG, "qg_ensemble_config: NULL argument");
+  form[0] = e->lanes > 0 && (size_t)e->lanes < e->h.size() ? e->lanes : (int32_t)e->h.size();
+  form[1] = e->pdl;
+  form[2] = e->lean;
+  form[3] = e->tuned;
+  if (ms_per_step) *ms_per_step = e->tuned_ms;
   return QG_OK;
 }
 

@@ -74,7 +74,7 @@ __host__ __device__ __forceinline__ int my_of_r(const Geom& g, int r) { return r
 __host__ __device__ __forceinline__ int row_of_r(const Geom& g, int r) { return r <= g.K ? r : g.n + r - g.Ny; }
 
 constexpr int kMaxIn = 12;   // max fields entering one row pass
-constexpr int kMaxOut = 6;   // max fields leaving one row pass
+constexpr int kMaxOut = 8;   // max fields leaving one row pass
 constexpr int kMaxDer = 12;  // max derived fields leaving one column pass
 constexpr int kMaxFwd = 8;   // max fields entering one column pass
 constexpr int kMaxY = 8;     // row-pass output arrays of a handle
@@ -102,6 +102,10 @@ enum RowProg : int {
   RP_DSMAG = 4,   // RP_SMAG at grid and test level
   RP_SCALE = 5,   // f_i * factor(x, y) for each input (Brinkman, sponge)
   RP_COPY = 6,    // identity (forward transform of a physical field, or inverse to physical)
+  // the adjoint's fused passes (register-resident kernels): the step's products of one stage with its physical
+  // fields kept (RP_ADJ_FWD), and the transposed products of an adjoint field with kept fields (RP_ADJ_REV)
+  RP_ADJ_FWD = 7,
+  RP_ADJ_REV = 8,
 };
 
 // Column-pass operations.
@@ -117,6 +121,7 @@ enum ColOp : int {
   CO_AB2CN_COMBINE = 7,  // as CO_AB2CN from stored J, D, F_obs and the Germano partial sums
   CO_AB2CN_FINAL = 8,    // forward s = dt rate chi_s Z; w^{t+1} = w* - s
   CO_FORWARD2 = 9,       // forward two fields: the first to w0, the second to w0b (the adjoint's paired transforms)
+  CO_FORWARD_N = 10,     // forward nfwd fields, field f's kept band to fout[f] (the adjoint's transform batches)
 };
 
 struct RowDesc {
@@ -131,7 +136,17 @@ struct RowDesc {
   void* phys_out;
   const void* phys_in2;  // RP_COPY: a second physical field, transformed with the first (Hermitian pair)
   void* phys_out2;       // RP_COPY: the second field of an inverse pair
+  int npair;             // RP_COPY, register-resident kernels: > 0 transforms npair pairs in one launch, pair p
+                         // taking physical fields pin[2p], pin[2p + 1] to out[2p], out[2p + 1] (in_phys), or
+                         // mixed in[2p], in[2p + 1] to pout[2p], pout[2p + 1]; a NULL second field is skipped
+  const void* pin[kMaxOut];
+  void* pout[kMaxOut];
+  // RP_ADJ_FWD / RP_ADJ_REV: closure family (0 none, 1 Smagorinsky, 2 Leith) and the stage's physical fields
+  // u_total, v, w_x, w_y [, psi_xy, psi_xx - psi_yy] (written by RP_ADJ_FWD, read by RP_ADJ_REV)
+  int adj_kind;
+  void* pf[6];
   const void* factor;  // RP_SCALE: physical factor field
+  int test_kmax;       // dynamic closures: the test-level inputs vanish for k_x > test_kmax (0: not known)
   int check_finite;    // set *flag if a product is not finite
   int* flag;
   int* err;            // status bits of the bounds-checked debug build (NULL: not reported)
@@ -148,6 +163,7 @@ struct ColDesc {
   // spectral arrays
   void* w0;        // state w^n (read; written when store_w0)
   void* w0b;       // CO_FORWARD2: the second field's spectral band (written)
+  void* fout[kMaxFwd];  // CO_FORWARD_N: field f's spectral band (written)
   void* ws;        // RK stage state read when use_ws
   void* ws_out;    // RK stage state written when store_ws (a different array, so split passes never race)
   void* jh;        // dynamic closures: stored J_hat
@@ -185,6 +201,8 @@ struct ColDesc {
   const void* visc_y;  // exp(-nu ky^2 dt), per r
   double visc_mu;      // exp(-mu dt)
   int pdl;             // host side: launch with programmatic stream serialisation
+  int lean;            // host side, FP32 Germano reduction: 0 = lean form where it makes one wave, 1 = lean form
+                       // whenever it fits, 2 = never (the ensemble tuner's choice)
   int* flag;           // stop flag checked at entry (NULL: always run)
   int* err;            // status bits raised by bounded waits that give up (NULL: not reported)
   int stall_cta1;      // failure-handling test only (0 otherwise): CTA stall_cta1 - 1 arms its first tile's

@@ -405,6 +405,15 @@ class QGEnsemble:
     def step(self, nsteps: int = 1) -> None:
         check(load().qg_ensemble_step(self.e, int(nsteps)), "qg_ensemble_step")
 
+    def config(self) -> dict:
+        """The launch form the tuner chose (qg_ensemble_config)."""
+        form = (C.c_int32 * 4)()
+        ms = C.c_double()
+        check(load().qg_ensemble_config(self.e, form, C.byref(ms)), "qg_ensemble_config")
+        return {"lanes": int(form[0]), "pdl": int(form[1]), "lean": int(form[2]),
+                "source": {0: "default", 1: "timed", 2: "cached"}.get(int(form[3]), str(form[3])),
+                "ms_per_step": ms.value}
+
     def sync(self) -> None:
         bad = C.c_int32(-1)
         rc = load().qg_ensemble_sync(self.e, C.byref(bad))

@@ -175,3 +175,41 @@ def test_ensemble_of_the_bench_mix_runs_and_matches_alone_for_sampled_members():
         s.step(3)
         assert np.array_equal(got[i], s.get_state()), i
         s.close()
+
+
+@pytest.mark.parametrize("lanes,pdl,lean", [(1, 0, 0), (3, 1, 0), (2, 0, 1), (7, 1, 2)])
+def test_fixed_launch_forms_equal_members_stepped_alone(lanes, pdl, lean, monkeypatch):
+    """Every launch form the tuner can pick (lanes of chained members, programmatic dependent launch, the lean
+    or register Germano reduction) leaves each member's arithmetic unchanged."""
+    monkeypatch.setenv("QG_ENSEMBLE_LANES", str(lanes))
+    monkeypatch.setenv("QG_ENSEMBLE_PDL", str(pdl))
+    monkeypatch.setenv("QG_ENSEMBLE_LEAN", str(lean))
+    seeds = list(range(11, 11 + len(MIXED)))
+    a = run_ensemble(MIXED, 9, seeds, chunks=(1, 3))
+    b = run_alone(MIXED, 9, seeds)
+    for i, (x, y) in enumerate(zip(a, b)):
+        assert np.array_equal(x, y), f"member {i}"
+
+
+def test_tuner_choice_is_reported_cached_and_restores_the_initial_state():
+    """The tuner times its candidates by stepping the members from their zero initial states, then puts them
+    back: an ensemble stepped without set_state equals fresh handles stepped from zero.  A second ensemble of
+    the same signature takes the choice from the cache."""
+    specs = MIXED[:4]
+    with qg.QGEnsemble(specs) as ens:
+        cfg = ens.config()
+        assert 1 <= cfg["lanes"] <= len(specs) and cfg["pdl"] in (0, 1) and cfg["lean"] in (0, 1, 2)
+        assert cfg["source"] in ("timed", "cached")
+        for m in ens.members:
+            assert m.diagnostics()["step"] == 0
+        ens.step(3)
+        ens.sync()
+        got = [m.get_state() for m in ens.members]
+    for sp, g in zip(specs, got):
+        args = {k: v for k, v in sp.items() if k != "n"}
+        with qg.QGSolver(sp["n"], **args) as s:
+            s.step(3)
+            assert np.array_equal(g, s.get_state())
+    with qg.QGEnsemble(specs) as ens2:
+        assert ens2.config()["source"] == "cached"
+        assert ens2.config()["lanes"] == cfg["lanes"]
