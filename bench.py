@@ -128,6 +128,84 @@ def algorithmic_bytes(wl, precision_fp32: bool):
 FIELD_TRAVERSALS_PER_STAGE = {S.NONE: 14, S.SMAG: 22, S.LEITH: 18, S.DSMAG: 43, S.DLEITH: 35}
 
 
+# 2-D transforms per RK3 step by closure (inverse + forward over the three stages, Brinkman 4, sponge 2) and the
+# cost of one real 2-D transform, 2.5 N^2 log2(N^2) flops: the arithmetic model of a step.
+TRANSFORMS_PER_STEP = {S.NONE: 21, S.SMAG: 33, S.LEITH: 27, S.DSMAG: 60, S.DLEITH: 48}
+
+
+def step_flop_model(wl) -> float:
+    n2 = wl.n * wl.n
+    return TRANSFORMS_PER_STEP[wl.closure] * 2.5 * n2 * math.log2(n2)
+
+
+def host_cpu():
+    """CPU model name and logical core count of this host (for the CPU baseline)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def streamfunction(w):
+    """psi = lap^-1 w with zero mean on [0, 2 pi)^2 (plain numpy; for the per-field error report)."""
+    n = w.shape[0]
+    wh = np.fft.rfft2(w)
+    mx = np.arange(n // 2 + 1)[None, :]
+    my = np.fft.fftfreq(n, 1.0 / n)[:, None]
+    k2 = (mx * mx + my * my).astype(float)
+    k2[0, 0] = 1.0
+    ph = -wh / k2
+    ph[0, 0] = 0.0
+    return np.fft.irfft2(ph, s=(n, n))
+
+
+def precision_errors(qg, wl, w0, steps, stream, scheme):
+    """Step the FP64 and FP32 forms side by side from w0 and report the FP32 form's error per field
+    (relative L2 of w and psi, relative E and Z at the end, and the dynamic coefficient C at every step)."""
+    sol = {p: qg.QGSolver.from_workload(wl, precision=p, stream=stream, scheme=scheme)
+           for p in (qg.QG_FP64, qg.QG_FP32)}
+    cs = {p: [] for p in sol}
+    for s in sol.values():
+        s.set_state(w0)
+    for _ in range(steps):
+        for p, s in sol.items():
+            s.step(1)
+            cs[p].append(s.diagnostics(raise_nonfinite=False)["coeff"])
+    a = sol[qg.QG_FP64].get_state()
+    b = sol[qg.QG_FP32].get_state()
+    d64 = sol[qg.QG_FP64].diagnostics()
+    d32 = sol[qg.QG_FP32].diagnostics()
+    for s in sol.values():
+        s.close()
+    c64 = np.array(cs[qg.QG_FP64])
+    c32 = np.array(cs[qg.QG_FP32])
+    act = c64 > 0
+    out = {"steps": steps, "w": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+           "psi": float(np.linalg.norm(streamfunction(b) - streamfunction(a)) / np.linalg.norm(streamfunction(a))),
+           "E": abs(d32["energy"] - d64["energy"]) / abs(d64["energy"]),
+           "Z": abs(d32["enstrophy"] - d64["enstrophy"]) / abs(d64["enstrophy"]),
+           "steps_with_C_positive": int(act.sum()), "C_final_fp64": float(c64[-1]), "C_final_fp32": float(c32[-1])}
+    if wl.closure in (S.DSMAG, S.DLEITH):
+        out["C_max_rel_diff"] = float(np.max(np.abs(c32[act] - c64[act]) / c64[act])) if act.any() else None
+        out["C_mean_fp64"] = float(c64[act].mean()) if act.any() else 0.0
+    return out
+
+
 def field_model_bytes(wl, precision_fp32: bool):
     """(row-pass bytes per launch, RK3 step bytes) in the full-field round-trip model.
 
@@ -414,8 +492,9 @@ def run_reference(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n, "closure": S.CLOSURE_NAMES[wl.closure], "scheme": args.scheme,
                    "eta": wl.eta},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} full {wl.n}^2 steps of the FP64 numpy oracle (bounded to ~{budget:.0f} s)"},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": f"{steps} full {wl.n}^2 steps of the FP64 numpy oracle "
+                                        f"(bounded to ~{budget:.0f} s)"}, **host_cpu()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -670,7 +749,9 @@ def run_ensemble_bench(args):
     wls = [all_wls[i] for i in ensemble_shard(len(all_wls), rank, world)]
     pts = sum(w.n * w.n for w in wls)
     stream = torch.cuda.Stream()
+    t_create = time.perf_counter()
     ens = qg.QGEnsemble.from_workloads(wls, precision=qg.QG_FP32, stream=stream)
+    ens_form = dict(ens.config(), create_s=time.perf_counter() - t_create)
     w0 = [w.omega0() for w in wls]
     for m, w in zip(ens.members, w0):
         m.set_state(w)
@@ -764,6 +845,7 @@ def run_ensemble_bench(args):
                        "parallelism": f"members split over {world} GPUs" if world > 1 else "single",
                        "l2": "working set ~1 GB > 126 MB L2 (no flush)",
                        "sequential_ms_per_step": seq_ms, "concurrency_speedup": seq_ms / ms,
+                       "launch_form": ens_form,
                        "all_finite": all(d["finite"] for d in diag)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
@@ -791,15 +873,21 @@ def m_launches(m) -> int:
 # ---------------------------------------------------------------------------
 ADJ = {"n": 256, "n_fr": 1024, "steps": 400, "obs_first": 100, "obs_every": 20, "checkpoint": 20, "c": 0.17,
        "seed": 5, "beta": 5.0, "U": 0.5, "radius": 0.4}
-def adj_metric(precision: str = "fp64") -> str:
-    return (f"grid-pt-steps/s of the loss gradient (forward + checkpointed adjoint), 256^2 Smagorinsky "
-            f"{precision.upper()} LES, 400 steps, MSE against a filtered 1024^2 run")
+ADJ_CLOSURES = {"dsmag": (S.DSMAG, "dynamic Smagorinsky"), "smag": (S.SMAG, "Smagorinsky")}
 
 
-def adjoint_workload():
+def adj_metric(precision: str = "fp64", closure: str = "dsmag") -> str:
+    return (f"grid-pt-steps/s of the loss gradient (forward + checkpointed adjoint), 256^2 "
+            f"{ADJ_CLOSURES[closure][1]} {precision.upper()} LES, 400 steps, MSE against a filtered 1024^2 run")
+
+
+def adjoint_workload(closure: str = "dsmag"):
+    """The adjoint configuration: a 256^2 island LES (dynamic Smagorinsky by default, the configuration's closure;
+    static Smagorinsky c_S = 0.17 with closure="smag"), gradients over 400 steps."""
     c = ADJ
-    les = S.Workload("adjoint256-smag", c["n"], "island", beta=c["beta"], U=c["U"], closure=S.SMAG, c=c["c"],
-                     radius=c["radius"], seed=c["seed"])
+    kind = ADJ_CLOSURES[closure][0]
+    les = S.Workload(f"adjoint256-{closure}", c["n"], "island", beta=c["beta"], U=c["U"], closure=kind,
+                     c=c["c"] if kind == S.SMAG else 0.0, radius=c["radius"], seed=c["seed"])
     fr = S.Workload("fr1024", c["n_fr"], "island", beta=c["beta"], U=c["U"], closure=S.NONE, radius=c["radius"],
                     seed=c["seed"])
     obs = list(range(c["obs_first"], c["steps"] + 1, c["obs_every"]))
@@ -807,8 +895,9 @@ def adjoint_workload():
 
 
 def adjoint_targets(qg, fr, obs, stream):
-    """The 1024^2 run (FP32, no closure) at the observed steps, filtered to 256^2 (Eq. 5), and its filtered start."""
-    s = qg.QGSolver.from_workload(fr, precision=qg.QG_FP32, stream=stream)
+    """The 1024^2 run (FP64, no closure: the form the oracle pins) at the observed steps, filtered to 256^2
+    (Eq. 5), and its filtered start."""
+    s = qg.QGSolver.from_workload(fr, precision=qg.QG_FP64, stream=stream)
     w0 = fr.omega0()
     s.set_state(w0)
     snaps = []
@@ -846,17 +935,18 @@ def run_adjoint_reference(args, budget):
     rank, _, _ = dist_env()
     if rank != 0:
         return
-    les, _, _ = adjoint_workload()
+    les, _, _ = adjoint_workload(args.closure)
     done, el = time_adjoint_oracle(les, budget)
     value = les.n * les.n * done / el
     line = {
-        "metric": adj_metric(args.precision), "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 1,
+        "metric": adj_metric(args.precision, args.closure), "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": 1,
         "steps": done,
         "warmup": 0, "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": "adjoint256", **ADJ},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward steps "
-                                   f"+ 1 full_step_vjp each) of the 256^2 LES, {el:.1f} s"},
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": "adjoint256", "closure": args.closure, **ADJ},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward "
+                                        f"steps + 1 full_step_vjp each) of the 256^2 LES, {el:.1f} s"}, **host_cpu()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -878,7 +968,7 @@ def run_adjoint_bench(args):
         from paper_2508_06678_gb300.build import build
         build()
     lib = load()
-    les, fr, obs = adjoint_workload()
+    les, fr, obs = adjoint_workload(args.closure)
     stream = torch.cuda.Stream()
     w0_les, targets = adjoint_targets(qg, fr, obs, stream)
     n, K, ce = les.n, ADJ["steps"], ADJ["checkpoint"]
@@ -1015,12 +1105,15 @@ def run_adjoint_bench(args):
             cpu = {"value": n * n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{done} steps of the FP64 numpy oracle's checkpointed gradient (2 forward steps + 1 "
                              f"full_step_vjp each) of the 256^2 LES, {el:.1f} s"}
+            cpu.update(host_cpu())
         line = {
-            "metric": adj_metric(args.precision), "value": value, "unit": UNIT, "n_gpus": world, "steps": reps,
+            "metric": adj_metric(args.precision, args.closure), "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": reps,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
             "data": "synthetic",
-            "config": {"workload": "adjoint256", **ADJ, "observed_steps": len(obs), "loss": loss,
+            "config": {"workload": "adjoint256", "closure": args.closure, **ADJ, "observed_steps": len(obs),
+                       "loss": loss, "dloss_dC": g.get("C"),
                        "grad_norm": float(lam.norm().item()), "dloss_dc": g["c"], "dloss_drate": g["sponge_rate"],
                        "ms_per_gradient": ms, "forward_ms_per_step": fwd_ms, "vjp_ms_per_step": vjp_ms,
                        "adjoint_over_forward": vjp_ms / fwd_ms,
@@ -1059,7 +1152,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 throughput / error leg")
     ap.add_argument("--fp64-steps", type=int, default=50)
-    ap.add_argument("--err-steps", type=int, default=100)
+    ap.add_argument("--err-steps", type=int, default=300,
+                    help="steps of the FP32-vs-FP64 error comparison (the configuration's 300)")
+    ap.add_argument("--closure", default="dsmag", choices=sorted(ADJ_CLOSURES),
+                    help="adjoint256 only: the LES closure (the configuration's dynamic Smagorinsky by default)")
+    ap.add_argument("--spinup", type=int, default=1000,
+                    help="untimed steps before the warm-up: the configuration times steps 1000-5000")
     ap.add_argument("--no-torch-context", action="store_true",
                     help="skip timing the torch.fft (cuFFT) form of the step beside libqg")
     args = ap.parse_args()
@@ -1106,8 +1204,9 @@ def main():
                                        scheme=scheme)
     w0 = wl.omega0()
     solver.set_state(w0)
-    solver.step(args.warmup)
+    solver.step(args.spinup + args.warmup)
     solver.sync()
+    spun = solver.diagnostics(raise_nonfinite=False)
 
     def barrier():
         if world > 1:
@@ -1215,8 +1314,9 @@ def main():
            "d2h_bytes_per_step": (wl.n * wl.n * esz + 56) / args.steps,
            "api": "qg_set_state(host) + qg_step(K) + qg_get_state(host) + qg_diagnostics"}
 
-    # ---- the FP64 form on the same workload: throughput, and the FP32 form's
-    # relative vorticity error against it after the same number of steps
+    # ---- the FP64 form on the same workload: throughput against its arithmetic roofline, and the FP32 form's
+    # error per field against it (the FP64 form is pinned to the oracle at 1e-12), on the workload's own field
+    # and on a rough seeded field (spectral peak N/8) that keeps the dynamic coefficient active from the start
     fp64 = None
     if fp32 and not args.no_fp64:
         s64 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP64, stream=stream, scheme=scheme)
@@ -1231,23 +1331,34 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / k64
-        s32 = qg.QGSolver.from_workload(wl, precision=qg.QG_FP32, stream=stream, scheme=scheme)
-        s64.set_state(w0)
-        s32.set_state(w0)
-        s64.step(args.err_steps)
-        s32.step(args.err_steps)
-        a = s64.get_state()
-        b = s32.get_state()
-        rel_err = float(np.linalg.norm(b - a) / np.linalg.norm(a))
-        d64 = s64.diagnostics()
-        d32 = s32.diagnostics()
-        s32.close()
         s64.close()
+        f64 = C.c_double()
+        f32 = C.c_double()
+        rc64 = lib.qg_probe_fma_rate(qg.QG_FP64, C.byref(f64), None)
+        rc32 = lib.qg_probe_fma_rate(qg.QG_FP32, C.byref(f32), None)
+        flops = step_flop_model(wl)
+        alu = None
+        if rc64 == 0 and f64.value > 0:
+            ach = flops / (ms64 / 1e3) / 1e12
+            alu = {"bound": "alu", "achieved": ach, "peak": f64.value / 1e12, "unit": "TFLOP/s",
+                   "frac": ach / (f64.value / 1e12), "peak_source": "measured FP64 FMA rate (qg_probe_fma_rate)",
+                   "flops_per_step": flops,
+                   "model": f"{TRANSFORMS_PER_STEP[wl.closure]} real 2-D transforms per step x 2.5 N^2 log2(N^2)",
+                   "hbm_model_frac": field_model_bytes(wl, False)[1] / (ms64 / 1e3) / 1e9
+                   / float(measured_peaks()[0].get("hbm_gbs", 6800.0))}
+        err_own = precision_errors(qg, wl, w0, args.err_steps, stream, scheme)
+        # the same parameters past the cape: the coast feeds the small scales and the closure is active
+        cape = S.Workload(wl.name.replace("island", "cape"), wl.n, "cape", beta=wl.beta, U=wl.U, closure=wl.closure,
+                          c=wl.c, dt=wl.dt, nu=wl.nu, mu=wl.mu, eta=wl.eta, sponge_rate=wl.sponge_rate, seed=wl.seed)
+        err_cape = precision_errors(qg, cape, cape.omega0(), args.err_steps, stream, scheme)
         fp64 = {"value": wl.n * wl.n / (ms64 / 1e3), "ms_per_step": ms64, "steps_timed": k64,
                 "fp32_speedup": ms64 / (ms / args.steps),
-                "fp32_rel_l2_err_vs_fp64": rel_err, "err_steps": args.err_steps,
-                "energy_rel_diff": abs(d32["energy"] - d64["energy"]) / abs(d64["energy"]),
-                "enstrophy_rel_diff": abs(d32["enstrophy"] - d64["enstrophy"]) / abs(d64["enstrophy"])}
+                "fp32_rel_l2_err_vs_fp64": err_own["w"], "err_steps": args.err_steps,
+                "energy_rel_diff": err_own["E"], "enstrophy_rel_diff": err_own["Z"],
+                "fp32_errors": {"workload": err_own, "same_parameters_past_the_cape": err_cape},
+                "roofline": alu,
+                "fma_tflops": {"fp64": f64.value / 1e12 if rc64 == 0 else None,
+                               "fp32": f32.value / 1e12 if rc32 == 0 else None}}
 
     torch_ctx = None
     if rank == 0 and scheme == 0 and fp32 and not args.no_torch_context:
@@ -1260,6 +1371,7 @@ def main():
             cpu = {"value": wl.n * wl.n * steps_c / el_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{steps_c} full {wl.n}^2 step(s) of the FP64 numpy oracle (single-threaded), "
                              f"{el_c:.1f} s"}
+            cpu.update(host_cpu())
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -1270,6 +1382,8 @@ def main():
                                                       if fp32 else ""),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "working set > 126 MB L2 (inputs larger than L2, no flush)",
+                       "timed_steps_from": args.spinup + args.warmup,
+                       "coeff_after_spinup": spun["coeff"],
                        "final_energy": diag["energy"], "final_coeff": diag["coeff"], "finite": diag["finite"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
             "torch_fft_context": torch_ctx,

@@ -105,7 +105,89 @@ def test_100_step_parity_fp32_cape(kind, n):
     gpu.step(100)
     err = rel(gpu.get_state(), ref.get_state())
     assert err < 2e-4, err
+    if kind in (S.DSMAG, S.DLEITH):
+        # the closure is active at the end of the run, in both implementations
+        assert ref.last_coeff > 0
+        assert gpu.diagnostics()["coeff"] == pytest.approx(ref.last_coeff, rel=2e-2)
     gpu.close()
+
+
+def streamfunction(w):
+    """psi = lap^-1 w on [0, 2 pi)^2 with zero mean (plain numpy)."""
+    n = w.shape[0]
+    wh = np.fft.rfft2(w)
+    mx = np.arange(n // 2 + 1)[None, :]
+    my = np.fft.fftfreq(n, 1.0 / n)[:, None]
+    k2 = (mx * mx + my * my).astype(float)
+    k2[0, 0] = 1.0
+    ph = -wh / k2
+    ph[0, 0] = 0.0
+    return np.fft.irfft2(ph, s=(n, n))
+
+
+def field_errors(got, d, ref):
+    """Relative error of each reported field against the oracle: w, psi, C, E, Z."""
+    r = ref.diagnostics()
+    w_ref = ref.get_state()
+    out = {"w": rel(got, w_ref), "psi": rel(streamfunction(got), streamfunction(w_ref)),
+           "E": abs(d["energy"] - r["energy"]) / r["energy"], "Z": abs(d["enstrophy"] - r["enstrophy"]) / r["enstrophy"]}
+    if ref.last_coeff > 0:
+        out["C"] = abs(d["coeff"] - ref.last_coeff) / ref.last_coeff
+    return out
+
+
+@pytest.mark.parametrize("kind", [S.SMAG, S.LEITH, S.DSMAG, S.DLEITH])
+def test_cape512_100_steps_fp64_and_fp32_against_the_oracle(kind):
+    """The closure sweep's own configuration (512^2 cape, beta = 10, U = 1, its seed and spectrum), 100 steps:
+    the FP64 form within 1e-11 of the oracle and the FP32 form within 2e-4 (relative L2 of w), per field
+    (w, psi, E, Z, and C for the dynamic closures, which are active by then)."""
+    wl = S.cape512(kind)
+    w0 = wl.omega0()
+    ref = O.QGOracle(wl.n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(kind, c=wl.c), O.Params())
+    ref.set_state(w0)
+    ref.step(100)
+    dynamic = kind in (S.DSMAG, S.DLEITH)
+    if dynamic:
+        assert ref.last_coeff > 0
+    for prec, tol, ctol in ((qg.QG_FP64, 1e-11, 1e-9), (qg.QG_FP32, 2e-4, 2e-2)):
+        with qg.QGSolver.from_workload(wl, precision=prec) as s:
+            s.set_state(w0)
+            s.step(100)
+            got = s.get_state()
+            d = s.diagnostics()
+        e = field_errors(got, d, ref)
+        assert e["w"] < tol, (prec, e)
+        assert e["psi"] < tol, (prec, e)
+        assert e["E"] < tol and e["Z"] < tol, (prec, e)
+        if dynamic:
+            assert d["coeff"] > 0 and e["C"] < ctol, (prec, e, d["coeff"], ref.last_coeff)
+
+
+@pytest.mark.slow
+def test_full_size_fp32_100_steps_against_the_oracle_closure_active():
+    """2048^2 dynamic Leith, FP32 form, 100 steps against the oracle with the closure active.  The island
+    workload's resolved flow leaves the Germano coefficient clipped to zero at this resolution, so the
+    same parameters run past the cape (coastal wall and cape, beta = 5, U = 0.5, nu = 1/200, the workload's
+    seeded field), where the penalised coast feeds the small scales and C > 0 from the fourth step on.  Relative
+    L2 of w and psi within 2e-4, E and Z within 2e-4, C within 2%.  The oracle takes several minutes here."""
+    base = S.island2048_dleith()
+    wl = S.Workload("cape2048-dleith", base.n, "cape", beta=base.beta, U=base.U, closure=S.DLEITH, seed=base.seed)
+    n = wl.n
+    w0 = wl.omega0()
+    ref = O.QGOracle(n, wl.L, wl.beta, wl.U, wl.mask(), wl.sponge_field(), O.Closure(wl.closure), O.Params())
+    ref.set_state(w0)
+    ref.step(100)
+    assert ref.last_coeff > 0
+    with qg.QGSolver.from_workload(wl, precision=qg.QG_FP32) as s:
+        s.set_state(w0)
+        s.step(100)
+        got = s.get_state()
+        d = s.diagnostics()
+    e = field_errors(got, d, ref)
+    assert d["coeff"] > 0
+    assert e["w"] < 2e-4 and e["psi"] < 2e-4, e
+    assert e["E"] < 2e-4 and e["Z"] < 2e-4, e
+    assert e["C"] < 2e-2, e
 
 
 @pytest.mark.parametrize("kind", [S.DSMAG, S.DLEITH])
