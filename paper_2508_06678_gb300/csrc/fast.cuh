@@ -147,6 +147,7 @@ template <typename T, int N> struct E16 {
   static constexpr int OFF3 = NP16 >= 2 ? 15 * 16 : 0;             // pass 3: NS = 256, R = 16 (N = 4096)
   static constexpr int OFFL = OFF3 + (NP16 >= 3 ? 15 * 256 : 0);   // last pass: NS = N / RLAST, R = RLAST
   static constexpr int TABLE = OFFL + (RLAST > 1 ? (RLAST - 1) * (N / RLAST) : 0);
+  static constexpr int NEX = NP16 + (RLAST > 1 ? 1 : 0) - 1;  // shared-memory exchanges of one transform
 
   // One Stockham pass; x in natural ownership on entry.  Non-last passes
   // exchange through buf (this sequence's padded slot area).
@@ -226,6 +227,7 @@ template <typename T, int N> struct E12 {
   static constexpr int BUF = N + N / 16;
   static constexpr int K = (N - 1) / 3;
   static constexpr int Kc = K + 1;
+  static constexpr int NEX = NP4 + (RLAST == 2 ? 1 : 0);  // shared-memory exchanges: radix-12 pass + radix-4 passes
   static_assert(N % 12 == 0 && is_pow2(N / 12) && N >= 384 && N <= 3072, "E12 engine: N must be 3 * 2^p, 384..3072");
 
   __device__ static __forceinline__ int pad(int i) { return i + (i >> 4); }

@@ -105,20 +105,15 @@ struct RowCtx {
   const Geom* g;
   int bad;
 
-  // inverse x-transform of the pair (A + i B) of half-spectrum rows; B may be null.  Columns beyond kmax are
-  // known to be zero (the test-filtered fields) and are not loaded.
-  __device__ __forceinline__ void inv_pair(C* x, const void* Av, const void* Bv, int kmax = E::K) {
+  // inverse x-transform of the pair (A + i B) of half-spectrum rows; B may be null
+  __device__ __forceinline__ void inv_pair(C* x, const void* Av, const void* Bv) {
     const C* A = reinterpret_cast<const C*>(Av) + (size_t)y * g->IP;
     const C* B = Bv ? reinterpret_cast<const C*>(Bv) + (size_t)y * g->IP : nullptr;
 #pragma unroll
     for (int m = 0; m < E::EL; ++m) {
       const int k = t + TT * m;
       C z = mk<C>(T(0), T(0));
-      if (k <= E::K && k > kmax) {
-        // zero column
-      } else if (k >= N - E::K && N - k > kmax) {
-        // zero column
-      } else if (k <= E::K) {
+      if (k <= E::K) {
         C a = A[k];
         C b = B ? B[k] : mk<C>(T(0), T(0));
         if (k == 0) {
@@ -139,6 +134,12 @@ struct RowCtx {
   // forward x-transform of (re, im) = two real rows, split, optional i k_x, store kept columns
   __device__ __forceinline__ void fwd_store(C* x, void* Av, void* Bv, bool dxa, bool dxb) {
     E::run(x, t, b0, b1, ph, tw, -1);
+    split_store(x, Av, Bv, dxa, dxb);
+  }
+
+  // split the forward transform of two real rows (re, im) into their half spectra, optional i k_x, store the
+  // kept columns
+  __device__ __forceinline__ void split_store(C* x, void* Av, void* Bv, bool dxa, bool dxb) {
     C* ub = ph ? b1 : b0;
     ph ^= 1;
 #pragma unroll
@@ -178,19 +179,19 @@ struct RowCtx {
 // Q = g w_y with g = |grad w| (Leith) or |S| (Smagorinsky); NONE forms J only.
 template <typename T, int N, bool SMAG, bool NONE>
 __device__ __forceinline__ void level_products(RowCtx<T, N>& cx, cplx_t<T>* x, const void* const* in, T* J, T* P,
-                                               T* Q, int kmax = Eng<T, N>::K) {
+                                               T* Q) {
   using C = cplx_t<T>;
   using E = Eng<T, N>;
-  cx.inv_pair(x, in[0], in[1], kmax);
+  cx.inv_pair(x, in[0], in[1]);
 #pragma unroll
   for (int m = 0; m < E::EL; ++m) {
     J[m] = x[m].x;  // u_total
     P[m] = x[m].y;  // v
   }
-  cx.inv_pair(x, in[2], in[3], kmax);  // (w_x, w_y)
+  cx.inv_pair(x, in[2], in[3]);  // (w_x, w_y)
   if constexpr (SMAG) {
     C s[E::EL];
-    cx.inv_pair(s, in[4], in[5], kmax);
+    cx.inv_pair(s, in[4], in[5]);
 #pragma unroll
     for (int m = 0; m < E::EL; ++m) {
       T j, p, q;
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, Occ<T>::row) row_fast_kern
         T Qk[E::EL];
 #pragma unroll
         for (int m = 0; m < E::EL; ++m) Qk[m] = Q[m];
-        level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q, d.test_kmax > 0 ? d.test_kmax : E::K);
+        level_products<T, N, smag, false>(cx, x, d.in + per, J, P, Q);
 #pragma unroll
         for (int m = 0; m < E::EL; ++m) x[m] = mk<C>(Qk[m], Q[m]);
         cx.fwd_store(x, d.out[2], d.out[5], false, false);
@@ -901,7 +902,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
       A[m] = cscale(A[m], scale);
     }
     const T ksc = T(g.kscale);
-    int used = 0;  // fields transformed so far (alternates the two stages)
+    // Three shared buffers rotate between the transform's two exchange buffers and the output tile of the TMA
+    // store: the tile goes to the exchange buffer the transform's last exchange did not use (so no barrier is
+    // needed before it is written), and the next field avoids the buffer whose store may still be reading.
+    // t1, t2: the buffers of the previous two fields' tiles (-1: none).  The first exchange buffer is never
+    // either of them; the second may be t2, whose store the lead thread waits for before the first exchange's
+    // barrier, which every thread passes before it writes the second exchange buffer.
+    unsigned char* const bufs[3] = {sbase, sbase + SB, sbase + 2 * SB};
+    int t1 = -1, t2 = -1;
 #pragma unroll 1
     for (int q = 0; q < d.nder; ++q) {
       const int code = d.der[q];
@@ -947,18 +955,25 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
           break;
       }
 #undef QG_KY
-      C* st = stage[used & 1];
-      ++used;
-      // the store issued from this stage two fields ago has finished reading it
+      int e2 = t2;
+      if (e2 < 0 || e2 == t1) e2 = t1 == 1 ? 2 : 1;
+      int e1 = 0;
+      while (e1 == t1 || e1 == e2) ++e1;
+      const int tb = (E::NEX % 2 == 0) ? e1 : e2;
+      C* b0 = reinterpret_cast<C*>(bufs[e1]);
+      C* b1 = reinterpret_cast<C*>(bufs[e2]);
+      C* st = reinterpret_cast<C*>(bufs[tb]);
+      // at most the previous field's store is still reading (its tile is in neither exchange buffer)
       if (lead) tma::wait_group_read<1>();
-      __syncthreads();
       ph = 0;
-      E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, +1);
-      __syncthreads();  // all exchange reads of the stage are done
+      E::run(x, t, b0 + c * CP, b1 + c * CP, ph, twb, +1);
+      // the tile buffer's last reads in this transform came before its last exchange's barrier
 #pragma unroll
       for (int m = 0; m < E::EL; ++m) st[(t + TT * m) * W + c] = x[m];
       tma::fence_proxy_async();
       __syncthreads();
+      t2 = t1;
+      t1 = tb;
       if (lead) {
         for (int bx = 0; bx < NBOX; ++bx)
           tma::store_2d(&tm.out[q], 2 * c0, bx * BR,

@@ -225,6 +225,11 @@ struct qg_handle {
   double* adj_dots = nullptr;
   cudaGraphExec_t adj_graph = nullptr;  // one adjoint step, captured after its first eager run
   bool adj_graph_tried = false;
+  // side branch of the adjoint step: a second stream, its fork event and join events (one per pending branch)
+  cudaStream_t adj_side = nullptr;
+  cudaEvent_t adj_fork_ev = nullptr;
+  cudaEvent_t adj_join_ev[8] = {};
+  int adj_njoin = 0;
   int32_t adj_graph_launches[QG_NUM_KCLASS] = {};
   void* tw = nullptr;
   void* ptw = nullptr;  // per-pass twiddle table of the power-of-two kernels
@@ -266,6 +271,11 @@ struct qg_handle {
   std::vector<cudaEvent_t> pool;
 
   ~qg_handle() {
+    if (adj_side) cudaStreamSynchronize(adj_side);
+    if (adj_side) cudaStreamDestroy(adj_side);
+    if (adj_fork_ev) cudaEventDestroy(adj_fork_ev);
+    for (cudaEvent_t ev : adj_join_ev)
+      if (ev) cudaEventDestroy(ev);
     if (step_graph) cudaGraphExecDestroy(step_graph);
     if (adj_graph) cudaGraphExecDestroy(adj_graph);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -524,7 +534,6 @@ int enqueue_step(qg_handle* h) {
     r.nin = h->nin;
     r.nout = h->nout;
     r.dx_mask = h->dx_mask;
-    r.test_kmax = h->test_kmax;
     r.check_finite = 1;
     for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
     for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
@@ -656,7 +665,6 @@ int enqueue_step_ab2(qg_handle* h) {
   r.nin = h->nin;
   r.nout = h->nout;
   r.dx_mask = h->dx_mask;
-  r.test_kmax = h->test_kmax;
   r.check_finite = 1;
   for (int i = 0; i < h->nin; ++i) r.in[i] = h->X[i];
   for (int i = 0; i < h->nout; ++i) r.out[i] = h->Y[i];
@@ -780,6 +788,37 @@ int adj_alloc(qg_handle* h) {
   return QG_OK;
 }
 
+// Side branches.  Work enqueued between adj_fork and adj_unfork runs on the handle's second stream, after
+// everything enqueued on the main stream before the fork; adj_unfork returns a join slot, and adj_join(slot) makes
+// the main stream wait for that branch.  Branches among themselves run in order on the side stream.  Used for
+// launches off the adjoint's critical path (the stages' coefficient derivatives, an accumulation, parts of the
+// sponge transpose), so they overlap the main chain of dependent launches.
+int adj_fork(qg_handle* h, cudaStream_t* saved) {
+  if (!h->adj_side) {
+    CK(cudaStreamCreateWithFlags(&h->adj_side, cudaStreamNonBlocking), "adjoint: side stream");
+    CK(cudaEventCreateWithFlags(&h->adj_fork_ev, cudaEventDisableTiming), "adjoint: fork event");
+    for (cudaEvent_t& ev : h->adj_join_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "adjoint: join");
+  }
+  CK(cudaEventRecord(h->adj_fork_ev, h->stream), "adjoint: fork");
+  CK(cudaStreamWaitEvent(h->adj_side, h->adj_fork_ev, 0), "adjoint: fork wait");
+  *saved = h->stream;
+  h->stream = h->adj_side;
+  return QG_OK;
+}
+
+int adj_unfork(qg_handle* h, cudaStream_t saved, int* slot) {
+  h->stream = saved;
+  if (h->adj_njoin >= 8) return fail(QG_ERR_ARG, "adjoint: too many pending branches");
+  *slot = h->adj_njoin++;
+  CK(cudaEventRecord(h->adj_join_ev[*slot], h->adj_side), "adjoint: join record");
+  return QG_OK;
+}
+
+int adj_join(qg_handle* h, int slot) {
+  CK(cudaStreamWaitEvent(h->stream, h->adj_join_ev[slot], 0), "adjoint: join");
+  return QG_OK;
+}
+
 // spectral band (T F[f], mean removed if asked) of a physical field
 int adj_to_spec(qg_handle* h, const void* P, void* S, bool zero_mean) {
   RowDesc r{};
@@ -857,7 +896,9 @@ int adj_to_spec_many(qg_handle* h, std::initializer_list<const void*> P, std::in
 
 // physical fields of derived spectra (codes D_W, D_U (with U), D_V, D_WX, D_WY, D_PXY, D_PD) of a spectral
 // state: one derive pass, then row passes in pairs
-int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, std::initializer_list<void*> P) {
+// m0: first of the mixed scratch arrays the passes use (a side branch takes ones the main chain leaves alone)
+int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, std::initializer_list<void*> P,
+                int m0 = 0) {
   ColDesc c = col_base(h);
   c.pdl = 1;
   c.op = CO_DERIVE;
@@ -865,7 +906,7 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
   c.nder = 0;
   for (int code : codes) {
     c.der[c.nder] = code;
-    c.dout[c.nder] = h->adj_M[c.nder];
+    c.dout[c.nder] = h->adj_M[m0 + c.nder];
     ++c.nder;
   }
   int rc = run_col(h, c, QG_K_ADJ_COL, false);
@@ -880,7 +921,7 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
     r.out_phys = 1;
     r.npair = (int)(dst.size() + 1) / 2;
     for (size_t i = 0; i < dst.size(); ++i) {
-      r.in[i] = h->adj_M[i];
+      r.in[i] = h->adj_M[m0 + i];
       r.pout[i] = dst[i];
     }
     return run_row(h, r, QG_K_ADJ_ROW, false);
@@ -892,8 +933,8 @@ int adj_to_phys(qg_handle* h, const void* S, std::initializer_list<int> codes, s
     r.prog = RP_COPY;
     r.nin = two ? 2 : 1;
     r.nout = 1;
-    r.in[0] = h->adj_M[i];
-    r.in[1] = two ? h->adj_M[i + 1] : nullptr;
+    r.in[0] = h->adj_M[m0 + i];
+    r.in[1] = two ? h->adj_M[m0 + i + 1] : nullptr;
     r.out_phys = 1;
     r.phys_out = dst[i];
     r.phys_out2 = two ? dst[i + 1] : nullptr;
@@ -1051,6 +1092,20 @@ int adj_derive(qg_handle* h, const void* S, std::initializer_list<int> codes, in
     ++c.nder;
   }
   return run_col(h, c, QG_K_ADJ_COL, false);
+}
+
+// the exact Brinkman factor applied in one row pass to the pair adj_M[0], adj_M[1] (in place)
+int adj_brinkman_row(qg_handle* h) {
+  RowDesc r{};
+  r.pdl = 1;
+  r.prog = RP_SCALE;
+  r.nin = r.nout = 2;
+  r.in[0] = h->adj_M[0];
+  r.in[1] = h->adj_M[1];
+  r.out[0] = h->adj_M[0];  // each row is read in full before it is written
+  r.out[1] = h->adj_M[1];
+  r.factor = h->fac_b;
+  return run_row(h, r, QG_K_ADJ_ROW, false);
 }
 
 // the row and column passes of the fused reverse products once adj_M[0..2] hold lam, lam_x, lam_y
@@ -1229,6 +1284,29 @@ int adj_reverse_stage(qg_handle* h, int kind, bool dyn, double C, const void* Sl
   const double dt = h->par.dt, bd = b * dt;
   const int f0 = kAdjStageP + 6 * slot;  // the stage's fields, kept by the forward recomputation
   int rc = QG_OK;
+  int cslot = -1;
+  if (kind != AK_NONE) {
+    // derivative in C, on a side branch: sum over points of lam * T div(g grad ws) (Parseval over the band)
+    cudaStream_t main_st;
+    rc = adj_fork(h, &main_st);
+    if (!rc)
+      rc = adj_combine(h, S[18], false, false,
+                       {{S[kAdjStageS + 2 * slot], AM_IX, 1.0}, {S[kAdjStageS + 2 * slot + 1], AM_IY, 1.0}});
+    if (!rc) {
+      const double n2 = double(h->g.n) * double(h->g.n);
+      Bracket br(h, QG_K_ADJ_PW);
+      const cudaError_t e =
+          h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots,
+                                               h->adj_dots + kAdjDotBlocks + slot, h->stream)
+                  : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
+                                                h->adj_dots + kAdjDotBlocks + slot, h->stream);
+      br.done();
+      if (e != cudaSuccess) rc = cuda_fail(e, "adjoint: C derivative");
+    }
+    const int urc = adj_unfork(h, main_st, &cslot);
+    if (rc) return rc;
+    if (urc) return urc;
+  }
   if (h->fast) {
     rc = adj_derive(h, Slam, {D_W, D_WX, D_WY}, 0);
     if (!rc) rc = adj_fused_rev_tail(h, kind, f0);
@@ -1278,19 +1356,10 @@ int adj_reverse_stage(qg_handle* h, int kind, bool dyn, double C, const void* Sl
     CK(e, "adjoint: stage combine");
   }
   if (kind != AK_NONE) {
-    // derivative in C: sum over points of lam * T div(g grad ws) (Parseval over the band)
-    rc = adj_combine(h, S[18], false, false,
-                     {{S[kAdjStageS + 2 * slot], AM_IX, 1.0}, {S[kAdjStageS + 2 * slot + 1], AM_IY, 1.0}});
-    if (rc) return rc;
-    const double n2 = double(h->g.n) * double(h->g.n);
-    Bracket br(h, QG_K_ADJ_PW);
-    const cudaError_t e =
-        h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots,
-                                             h->adj_dots + kAdjDotBlocks + slot, h->stream)
-                : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
-                                              h->adj_dots + kAdjDotBlocks + slot, h->stream);
-    br.done();
-    CK(e, "adjoint: C derivative");
+    if (cslot >= 0) {
+      rc = adj_join(h, cslot);
+      if (rc) return rc;
+    }
     if (dyn) return adj_reverse_germano(h, kind, Slam_out, slot);
   }
   return QG_OK;
@@ -1308,6 +1377,7 @@ int adj_step(qg_handle* h) {
   const double C = kind == AK_NONE || dyn ? 0.0 : h->static_coeff;
   const double dt = h->par.dt;
   double* dots = h->adj_dots + kAdjDotBlocks;
+  h->adj_njoin = 0;
   CK(cudaMemsetAsync(dots, 0, (kAdjScalars + 12) * sizeof(double), h->stream), "adjoint: dots");
   static const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
   // forward: w0 -> w1 -> w2 -> w3 (S[0..3]), viscous factor, Brinkman -> S[4]
@@ -1316,7 +1386,24 @@ int adj_step(qg_handle* h) {
     rc = adj_forward_stage(h, kind, dyn, C, S[0], S[s], S[s + 1], A[s], B[s], s);
   if (!rc) rc = adj_combine(h, S[3], false, false, {{S[3], AM_VISC, 1.0}});
   if (rc) return rc;
-  if (h->fac_b) {
+  if (h->fac_b && h->fast) {
+    // the forward step's own Brinkman passes: (u_total, v) derived, scaled by the exact factor in one row pass,
+    // curl taken in the column pass that transforms them
+    rc = adj_derive(h, S[3], {D_U, D_V}, 0);
+    if (!rc) rc = adj_brinkman_row(h);
+    if (!rc) {
+      ColDesc c = col_base(h);
+      c.pdl = 1;
+      c.op = CO_CURL;
+      c.nfwd = 2;
+      c.fin[0] = h->adj_M[0];
+      c.fin[1] = h->adj_M[1];
+      c.w0 = S[4];
+      c.store_w0 = 1;
+      c.nder = 0;
+      rc = run_col(h, c, QG_K_ADJ_COL, false);
+    }
+  } else if (h->fac_b) {
     rc = adj_to_phys(h, S[3], {D_U, D_V}, {P[0], P[1]});
     if (!rc) rc = adj_scale(h, h->fac_b, P[0], 1.0, P[9], P[1], 1.0, P[10]);  // chi-factor times (u_total, v)
     if (!rc) rc = adj_to_spec_many(h, {P[9], P[10]}, {S[8], S[9]});
@@ -1329,26 +1416,63 @@ int adj_step(qg_handle* h) {
   // reverse: final projection (2/3 band, zero mean)
   void* lam = S[5];
   void* lam2 = S[6];
+  // the sponge's forward field w5 in physical space (a side branch, beside the final projection's transpose)
+  int w5slot = -1;
+  if (h->fac_s) {
+    cudaStream_t main_st;
+    rc = adj_fork(h, &main_st);
+    if (!rc) rc = adj_to_phys(h, S[4], {D_W}, {P[0]}, kAdjNM - 1);  // the last mixed array: the main chain's
+                                                                     // transforms here use the first ones
+    const int urc = adj_unfork(h, main_st, &w5slot);
+    if (rc) return rc;
+    if (urc) return urc;
+  }
   rc = adj_to_spec(h, P[18], lam, true);
+  int dotslot = -1;
   if (!rc && h->fac_s) {
     // w6 = T F[s w5]: d/drate = sum lam * (-chi_s dt s) * w5; lam <- T F[s lam]
-    rc = adj_to_phys(h, S[4], {D_W}, {P[0]});
-    if (!rc) rc = adj_to_phys(h, lam, {D_W}, {P[6]});
+    rc = adj_to_phys(h, lam, {D_W}, {P[6]});
+    if (!rc) rc = adj_join(h, w5slot);
     if (!rc) rc = adj_scale(h, h->fac_s, P[0], 1.0, P[1], P[6], 1.0, P[2]);
     if (rc) return rc;
     if (h->chi_s) {
-      Bracket br(h, QG_K_ADJ_PW);
-      const cudaError_t e =
-          h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                               dots + 3, h->stream)
-                  : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                                dots + 3, h->stream);
-      br.done();
-      CK(e, "adjoint: sponge-rate derivative");
+      // the sponge-rate derivative on a side branch (P[6] and P[1] are not written again in this step)
+      cudaStream_t main_st;
+      rc = adj_fork(h, &main_st);
+      if (!rc) {
+        Bracket br(h, QG_K_ADJ_PW);
+        const cudaError_t e =
+            h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                                 dots + 3, h->stream)
+                    : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
+                                                  dots + 3, h->stream);
+        br.done();
+        if (e != cudaSuccess) rc = cuda_fail(e, "adjoint: sponge-rate derivative");
+      }
+      const int urc = adj_unfork(h, main_st, &dotslot);
+      if (rc) return rc;
+      if (urc) return urc;
     }
     rc = adj_to_spec(h, P[2], lam, false);
   }
-  if (!rc && h->fac_b) {
+  if (!rc && h->fac_b && h->fast) {
+    // w5 = T (d_x (f v) - d_y (f u)): lam <- -conj(dv) F[f lam_x] + conj(du) F[f lam_y], the scaling in one row pass
+    rc = adj_derive(h, lam, {D_WX, D_WY}, 0);
+    if (!rc) rc = adj_brinkman_row(h);
+    if (!rc) {
+      ColDesc c = col_base(h);
+      c.pdl = 1;
+      c.op = CO_FORWARD_N;
+      c.nfwd = 2;
+      c.fin[0] = h->adj_M[0];
+      c.fin[1] = h->adj_M[1];
+      c.fout[0] = S[8];
+      c.fout[1] = S[9];
+      c.nder = 0;
+      rc = run_col(h, c, QG_K_ADJ_COL, false);
+    }
+    if (!rc) rc = adj_combine(h, lam, false, false, {{S[8], AM_CV, -1.0}, {S[9], AM_CU, 1.0}});
+  } else if (!rc && h->fac_b) {
     // w5 = T (d_x (f v) - d_y (f u)): lam <- conj(dv) F[f (-lam_x)] - conj(du) F[f (-lam_y)]
     rc = adj_to_phys(h, lam, {D_WX, D_WY}, {P[7], P[8]});
     if (!rc) rc = adj_scale(h, h->fac_b, P[7], -1.0, P[9], P[8], -1.0, P[10]);
@@ -1356,15 +1480,29 @@ int adj_step(qg_handle* h) {
     if (!rc) rc = adj_combine(h, lam, false, false, {{S[8], AM_CV, 1.0}, {S[9], AM_CU, -1.0}});
   }
   if (!rc) rc = adj_combine(h, lam, false, false, {{lam, AM_VISC, 1.0}});
-  if (!rc) rc = adj_combine(h, S[7], false, false, {});
-  // the three stages in reverse: w_{s+1} = a_s w0 + b_s (w_s + dt L(w_s))
+  // the sponge-rate branch reads P[6], which the generic kernels' reverse stages overwrite
+  if (!rc && dotslot >= 0) rc = adj_join(h, dotslot);
+  dotslot = -1;
+  // the three stages in reverse: w_{s+1} = a_s w0 + b_s (w_s + dt L(w_s)); the a_s lam share of w0's gradient
+  // accumulates in S[7] on a side branch, joined before the next stage overwrites that lam
+  bool s7_set = false;
   for (int s = 2; s >= 0 && !rc; --s) {
-    if (A[s] != 0.0) rc = adj_combine(h, S[7], true, false, {{lam, AM_ONE, A[s]}});
+    int accslot = -1;
+    if (A[s] != 0.0) {
+      cudaStream_t main_st;
+      rc = adj_fork(h, &main_st);
+      if (!rc) rc = adj_combine(h, S[7], s7_set, false, {{lam, AM_ONE, A[s]}});
+      const int urc = adj_unfork(h, main_st, &accslot);
+      if (!rc) rc = urc;
+      s7_set = true;
+    }
     if (!rc) rc = adj_reverse_stage(h, kind, dyn, C, lam, lam2, B[s], s);
+    if (!rc && accslot >= 0) rc = adj_join(h, accslot);
     std::swap(lam, lam2);
   }
-  if (!rc) rc = adj_combine(h, S[7], true, true, {{lam, AM_ONE, 1.0}});
+  if (!rc) rc = adj_combine(h, S[7], s7_set, true, {{lam, AM_ONE, 1.0}});
   if (!rc) rc = adj_to_phys(h, S[7], {D_W}, {P[18]});
+  if (!rc && dotslot >= 0) rc = adj_join(h, dotslot);
   return rc;
 }
 
@@ -1372,6 +1510,7 @@ int adj_step(qg_handle* h) {
 void adj_build_graph(qg_handle* h) {
   h->adj_graph_tried = true;
   if (!h->stream || getenv("QG_NO_GRAPH")) return;
+  if (h->adj_side) cudaStreamSynchronize(h->adj_side);  // the eager step's branches are done before capture
   int32_t saved[QG_NUM_KCLASS];
   memcpy(saved, h->launches, sizeof(saved));
   cudaGraph_t g = nullptr;

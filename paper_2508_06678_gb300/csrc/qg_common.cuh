@@ -146,7 +146,6 @@ struct RowDesc {
   int adj_kind;
   void* pf[6];
   const void* factor;  // RP_SCALE: physical factor field
-  int test_kmax;       // dynamic closures: the test-level inputs vanish for k_x > test_kmax (0: not known)
   int check_finite;    // set *flag if a product is not finite
   int* flag;
   int* err;            // status bits of the bounds-checked debug build (NULL: not reported)
