@@ -201,7 +201,17 @@ def precision_errors(qg, wl, w0, steps, stream, scheme):
            "Z": abs(d32["enstrophy"] - d64["enstrophy"]) / abs(d64["enstrophy"]),
            "steps_with_C_positive": int(act.sum()), "C_final_fp64": float(c64[-1]), "C_final_fp32": float(c32[-1])}
     if wl.closure in (S.DSMAG, S.DLEITH):
-        out["C_max_rel_diff"] = float(np.max(np.abs(c32[act] - c64[act]) / c64[act])) if act.any() else None
+        # per step where the FP64 coefficient is positive: the largest relative difference (large where C itself
+        # is near the clip at 0), the relative L2 difference over those steps, and the largest difference as a
+        # fraction of the largest coefficient
+        rel = np.abs(c32[act] - c64[act]) / c64[act] if act.any() else np.zeros(0)
+        out["C_max_rel_diff"] = float(rel.max()) if act.any() else None
+        out["C_median_rel_diff"] = float(np.median(rel)) if act.any() else None
+        out["C_steps_rel_diff_over_1pct"] = int((rel > 0.01).sum())
+        out["C_rel_l2_diff"] = (float(np.linalg.norm(c32[act] - c64[act]) / np.linalg.norm(c64[act]))
+                                if act.any() else None)
+        out["C_max_diff_over_max_C"] = (float(np.abs(c32[act] - c64[act]).max() / c64[act].max())
+                                        if act.any() else None)
         out["C_mean_fp64"] = float(c64[act].mean()) if act.any() else 0.0
     return out
 

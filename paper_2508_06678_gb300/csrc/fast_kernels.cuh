@@ -70,6 +70,13 @@ template <typename T, int N> __host__ __device__ constexpr int col_stage_bytes()
 template <typename T, int N> constexpr bool lean_fits() {
   return sizeof(T) == 4 && 3 * (2 * col_stage_bytes<T, N>() + 2048) <= 227 * 1024;
 }
+// column ops whose FFTs use the packed FP32 butterflies (bit op set): all but the dynamic combine and the final
+// passes (CO_DYN_COMBINE, CO_FORWARD, CO_AB2CN_FINAL), which measured 0.3-1.1 us faster per launch in the scalar
+// form at 2048^2 (the row passes and the Germano reduction gain 7% and 6% from packing)
+#ifndef QG_PACKED_COL_MASK
+#define QG_PACKED_COL_MASK 0xFED7
+#endif
+template <int OP> constexpr bool col_packed() { return (QG_PACKED_COL_MASK >> OP) & 1; }
 // bounded device waits: about one second of SM clocks
 constexpr long long kWaitCycles = 2000000000LL;
 
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
 #pragma unroll
       for (int m = 0; m < E::EL; ++m) x[m] = st[(t + TT * m) * W + c];
       ph = 0;
-      E::run(x, t, xbuf + c * CP, st + c * CP, ph, twb, -1);
+      E::template run<col_packed<OP>()>(x, t, xbuf + c * CP, st + c * CP, ph, twb, -1);
       // every thread is done with this stage: hand it to the TMA for field f + NSTG
       tma::fence_proxy_async();
       __syncthreads();
@@ -966,7 +973,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, LEAN ? 3 : Occ<T, OP>::col
       // at most the previous field's store is still reading (its tile is in neither exchange buffer)
       if (lead) tma::wait_group_read<1>();
       ph = 0;
-      E::run(x, t, b0 + c * CP, b1 + c * CP, ph, twb, +1);
+      E::template run<col_packed<OP>()>(x, t, b0 + c * CP, b1 + c * CP, ph, twb, +1);
       // the tile buffer's last reads in this transform came before its last exchange's barrier
 #pragma unroll
       for (int m = 0; m < E::EL; ++m) st[(t + TT * m) * W + c] = x[m];
