@@ -133,9 +133,23 @@ FIELD_TRAVERSALS_PER_STAGE = {S.NONE: 14, S.SMAG: 22, S.LEITH: 18, S.DSMAG: 43, 
 TRANSFORMS_PER_STEP = {S.NONE: 21, S.SMAG: 33, S.LEITH: 27, S.DSMAG: 60, S.DLEITH: 48}
 
 
-def step_flop_model(wl) -> float:
+def transforms_per_step(wl, scheme: int = 0) -> float:
+    """Real 2-D transforms of one step, counted as (x passes + y passes) / 2 over the launch sequence: RK3 from
+    the table above (island with sponge); AB2CN (Eq. 4) evaluates the products once, so the stage's nin inverse
+    and nout forward transforms, the Brinkman pair (its x passes on u, v and chi u, chi v, its y passes forward)
+    and the sponge's field in and out."""
+    if scheme == 0:
+        return TRANSFORMS_PER_STEP[wl.closure]
+    nin = {S.NONE: 4, S.LEITH: 4, S.SMAG: 6, S.DLEITH: 8, S.DSMAG: 12}[wl.closure]
+    nout = {S.NONE: 1, S.LEITH: 3, S.SMAG: 3, S.DLEITH: 6, S.DSMAG: 6}[wl.closure]
+    mask = 1 if wl.geometry != "none" else 0
+    sponge = 1 if wl.sponge else 0
+    return nin + nout + 3 * mask + 2 * sponge
+
+
+def step_flop_model(wl, scheme: int = 0) -> float:
     n2 = wl.n * wl.n
-    return TRANSFORMS_PER_STEP[wl.closure] * 2.5 * n2 * math.log2(n2)
+    return transforms_per_step(wl, scheme) * 2.5 * n2 * math.log2(n2)
 
 
 def host_cpu():
@@ -1362,16 +1376,18 @@ def main():
         f32 = C.c_double()
         rc64 = lib.qg_probe_fma_rate(qg.QG_FP64, C.byref(f64), None)
         rc32 = lib.qg_probe_fma_rate(qg.QG_FP32, C.byref(f32), None)
-        flops = step_flop_model(wl)
+        flops = step_flop_model(wl, scheme)
         alu = None
         if rc64 == 0 and f64.value > 0:
             ach = flops / (ms64 / 1e3) / 1e12
             alu = {"bound": "alu", "achieved": ach, "peak": f64.value / 1e12, "unit": "TFLOP/s",
                    "frac": ach / (f64.value / 1e12), "peak_source": "measured FP64 FMA rate (qg_probe_fma_rate)",
                    "flops_per_step": flops,
-                   "model": f"{TRANSFORMS_PER_STEP[wl.closure]} real 2-D transforms per step x 2.5 N^2 log2(N^2)",
-                   "hbm_model_frac": field_model_bytes(wl, False)[1] / (ms64 / 1e3) / 1e9
-                   / float(measured_peaks()[0].get("hbm_gbs", 6800.0))}
+                   "model": f"{transforms_per_step(wl, scheme):g} real 2-D transforms per step x 2.5 N^2 log2(N^2)",
+                   "hbm_model_frac": (field_model_bytes(wl, False)[1] if scheme == 0 else
+                                      sum(a * b for a, b in algorithmic_bytes_ab2cn(wl, False).values()))
+                   / (ms64 / 1e3) / 1e9 / float(measured_peaks()[0].get("hbm_gbs", 6800.0)),
+                   "hbm_model": "full-field round trips" if scheme == 0 else "band storage"}
         err_own = precision_errors(qg, wl, w0, args.err_steps, stream, scheme)
         # the same parameters past the cape: the coast feeds the small scales and the closure is active
         cape = S.Workload(wl.name.replace("island", "cape"), wl.n, "cape", beta=wl.beta, U=wl.U, closure=wl.closure,

@@ -124,3 +124,16 @@ def test_torch_fft_context_step_is_the_oracle_step(kind):
     ref.step(5)
     a, b = ts.inv(wh).numpy(), ref.get_state()
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-12
+
+
+def test_transform_counts_per_step():
+    """Real 2-D transforms per step, (x passes + y passes) / 2 over the launch sequence: the RK3 table's dynamic
+    Leith entry (3 stages x (8 inverse + 6 forward) + Brinkman 4 + sponge 2) and the AB2CN count (one evaluation)."""
+    import bench
+    import synth as S
+    wl = S.island2048_dleith()
+    assert bench.transforms_per_step(wl, 0) == 3 * (8 + 6) + 4 + 2
+    assert bench.transforms_per_step(wl, 1) == (8 + 6) + 3 + 2
+    bare = S.Workload("b", 256, "none", beta=5.0, U=0.0, closure=S.NONE, sponge=False)
+    assert bench.transforms_per_step(bare, 1) == 4 + 1
+    assert bench.step_flop_model(wl, 1) < bench.step_flop_model(wl, 0)
