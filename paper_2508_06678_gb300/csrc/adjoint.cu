@@ -152,28 +152,105 @@ __device__ double adj_block_sum(double v, double* red) {
   return s;
 }
 
-// per-block partial of sum_k w_k Re(A conj B) over the stored band (w = 1 on the k_x = 0 column, else 2)
+// The block that counts itself in last: every block's thread 0 has stored its partial; after a fence it adds
+// one to the counter, and the block that sees kAdjDotBlocks - 1 there finds every partial stored.
+__device__ bool adj_last_block(unsigned* counter) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// sum of n partials in a fixed order (lane i takes i, i + 32, ..., then a shuffle tree); lane 0 holds it
+__device__ double adj_partials_sum(const double* partials, int n) {
+  const volatile double* p = partials;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += p[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// the last block's share of a single sum: out = scale * sum, then kappa if asked, and the counter reset
+__device__ void adj_dot_finish(const AdjDotOut& o) {
+  if (!adj_last_block(o.counter) || threadIdx.x >= 32) return;
+  const double s = adj_partials_sum(o.partials, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double v = o.scale * s;
+    o.out[0] = v;
+    if (o.kappa) o.kappa[0] = (o.C[0] > 0.0 && o.mm[0] > 0.0) ? v / (o.n2 * o.mm[0]) : 0.0;
+    *o.counter = 0u;
+  }
+}
+
+__device__ __forceinline__ double spec_weight(const Geom& g, size_t e, int& ok) {
+  const int c = (int)(e / g.SP), r = (int)(e - (size_t)c * g.SP);
+  ok = c < g.Kc && r < g.Ny;
+  return c == 0 ? 1.0 : 2.0;
+}
+
+// sum_k w_k Re(A conj B) over the stored band (w = 1 on the k_x = 0 column, else 2)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) adj_spec_dot_kernel(Geom g, const void* A, const void* B,
-                                                                double* partials) {
+__global__ void __launch_bounds__(kThreads) adj_spec_dot_kernel(Geom g, const void* A, const void* B, AdjDotOut o) {
   pdl_enter();
   __shared__ double red[kThreads / 32];
   const size_t total = (size_t)g.Kcp * g.SP;
   double s = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / g.SP), r = (int)(e - (size_t)c * g.SP);
-    if (c >= g.Kc || r >= g.Ny) continue;
+    int ok;
+    const double w = spec_weight(g, e, ok);
+    if (!ok) continue;
     const cplx_t<T> a = ld<T>(A, e), b = ld<T>(B, e);
-    s += (c == 0 ? 1.0 : 2.0) * (double(a.x) * double(b.x) + double(a.y) * double(b.y));
+    s += w * (double(a.x) * double(b.x) + double(a.y) * double(b.y));
   }
   s = adj_block_sum(s, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (threadIdx.x == 0) o.partials[blockIdx.x] = s;
+  adj_dot_finish(o);
 }
 
-// per-block partial of sum_i x_i y_i z_i over physical points
+// <H M> and <M M> in one pass (the two sums the separate dots would form, term by term); the last block adds
+// C = max(0, <HM> / <MM>)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) adj_germano_dots_kernel(Geom g, const void* H, const void* M,
+                                                                    AdjDotOut o) {
+  pdl_enter();
+  __shared__ double red[kThreads / 32];
+  const size_t total = (size_t)g.Kcp * g.SP;
+  double hm = 0.0, mm = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int ok;
+    const double w = spec_weight(g, e, ok);
+    if (!ok) continue;
+    const cplx_t<T> a = ld<T>(H, e), b = ld<T>(M, e);
+    hm += w * (double(a.x) * double(b.x) + double(a.y) * double(b.y));
+    mm += w * (double(b.x) * double(b.x) + double(b.y) * double(b.y));
+  }
+  hm = adj_block_sum(hm, red);
+  __syncthreads();  // red is reused
+  mm = adj_block_sum(mm, red);
+  if (threadIdx.x == 0) {
+    o.partials[blockIdx.x] = hm;
+    o.partials2[blockIdx.x] = mm;
+  }
+  if (!adj_last_block(o.counter) || threadIdx.x >= 32) return;
+  const double shm = adj_partials_sum(o.partials, gridDim.x);
+  const double smm = adj_partials_sum(o.partials2, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double a = o.scale * shm, b = o.scale * smm;
+    o.out[0] = a;
+    o.out[1] = b;
+    o.out[2] = b > 0.0 ? fmax(0.0, a / b) : 0.0;
+    *o.counter = 0u;
+  }
+}
+
+// sum_i x_i y_i z_i over physical points
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_phys_dot_kernel(size_t count, const void* X, const void* Y,
-                                                                const void* Z, double* partials) {
+                                                                const void* Z, AdjDotOut o) {
   pdl_enter();
   __shared__ double red[kThreads / 32];
   const T* x = reinterpret_cast<const T*>(X);
@@ -183,32 +260,8 @@ __global__ void __launch_bounds__(kThreads) adj_phys_dot_kernel(size_t count, co
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
     s += double(x[i]) * double(y[i]) * double(z[i]);
   s = adj_block_sum(s, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-__global__ void adj_scalar_kernel(int op, const double* x0, const double* x1, const double* x2, double n2,
-                                  double* out) {
-  pdl_enter();
-  if (threadIdx.x != 0) return;
-  if (op == AS_COEFF) {
-    out[0] = x1[0] > 0.0 ? fmax(0.0, x0[0] / x1[0]) : 0.0;
-  } else {
-    out[0] = (x0[0] > 0.0 && x1[0] > 0.0) ? x2[0] / (n2 * x1[0]) : 0.0;
-  }
-}
-
-cudaError_t launch_adj_scalar(int op, const double* x0, const double* x1, const double* x2, double n2, double* out,
-                              cudaStream_t st) {
-  return launch_pdl(true, adj_scalar_kernel, dim3(1), dim3(32), 0, st, op, x0, x1, x2, n2, out);
-}
-
-// out[0] = scale * sum of the partials, in a fixed order
-__global__ void adj_finish_kernel(const double* partials, int n, double scale, double* out) {
-  pdl_enter();
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) s += partials[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) out[0] = scale * s;
+  if (threadIdx.x == 0) o.partials[blockIdx.x] = s;
+  adj_dot_finish(o);
 }
 
 namespace {
@@ -236,23 +289,20 @@ cudaError_t launch_adj_scale(size_t count, const void* f, const void* x0, double
 }
 
 template <typename T>
-cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, double scale, double* partials,
-                                double* out, cudaStream_t st) {
-  const cudaError_t e = launch_pdl(true, adj_spec_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, g, A, B,
-                                   partials);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(true, adj_finish_kernel, dim3(1), dim3(32), 0, st, (const double*)partials, (int)kAdjDotBlocks, scale,
-                    out);
+cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, const AdjDotOut& o, cudaStream_t st) {
+  return launch_pdl(true, adj_spec_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, g, A, B, o);
 }
 
 template <typename T>
-cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, double scale,
-                                double* partials, double* out, cudaStream_t st) {
-  const cudaError_t e = launch_pdl(true, adj_phys_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, count, X, Y,
-                                   Z, partials);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(true, adj_finish_kernel, dim3(1), dim3(32), 0, st, (const double*)partials, (int)kAdjDotBlocks, scale,
-                    out);
+cudaError_t launch_adj_germano_dots(const Geom& g, const void* H, const void* M, const AdjDotOut& o,
+                                    cudaStream_t st) {
+  return launch_pdl(true, adj_germano_dots_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, g, H, M, o);
+}
+
+template <typename T>
+cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, const AdjDotOut& o,
+                                cudaStream_t st) {
+  return launch_pdl(true, adj_phys_dot_kernel<T>, dim3(kAdjDotBlocks), dim3(kThreads), 0, st, count, X, Y, Z, o);
 }
 
 #define QG_ADJ_INST(T)                                                                                         \
@@ -260,10 +310,12 @@ cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, cons
   template cudaError_t launch_adj_products<T>(size_t, const AdjProducts&, cudaStream_t);                       \
   template cudaError_t launch_adj_scale<T>(size_t, const void*, const void*, double, void*, const void*,       \
                                            double, void*, cudaStream_t);                                       \
-  template cudaError_t launch_adj_spec_dot<T>(const Geom&, const void*, const void*, double, double*, double*, \
+  template cudaError_t launch_adj_spec_dot<T>(const Geom&, const void*, const void*, const AdjDotOut&,         \
                                               cudaStream_t);                                                   \
-  template cudaError_t launch_adj_phys_dot<T>(size_t, const void*, const void*, const void*, double, double*,  \
-                                              double*, cudaStream_t);
+  template cudaError_t launch_adj_germano_dots<T>(const Geom&, const void*, const void*, const AdjDotOut&,     \
+                                                  cudaStream_t);                                               \
+  template cudaError_t launch_adj_phys_dot<T>(size_t, const void*, const void*, const void*, const AdjDotOut&, \
+                                              cudaStream_t);
 QG_ADJ_INST(float)
 QG_ADJ_INST(double)
 #undef QG_ADJ_INST

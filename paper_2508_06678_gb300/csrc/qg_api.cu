@@ -775,7 +775,8 @@ int adj_alloc(qg_handle* h) {
   for (auto& p : P) if (!rc) rc = dalloc(h, &p, phys_bytes);
   for (auto& p : M) if (!rc) rc = dalloc(h, &p, mixed_bytes);
   void* dots = nullptr;
-  if (!rc) rc = dalloc(h, &dots, sizeof(double) * (kAdjDotBlocks + kAdjScalars + 12));
+  // partials | dot results (kAdjScalars) | per-stage scalars (4 x 3) | second partials | counter (zeroed here)
+  if (!rc) rc = dalloc(h, &dots, sizeof(double) * (2 * kAdjDotBlocks + kAdjScalars + 12 + 1));
   if (!rc && h->fast) {
     const int BR = fast_box_rows(h->g.n);
     for (void* m : M) if (!rc) rc = add_tensor_map(h, m, h->W, BR);
@@ -1016,22 +1017,16 @@ AdjProducts adj_prod_desc(qg_handle* h, int kind, int mode, int f0, int lam = 6)
 // device scalars of stage s of a dynamic closure: <HM>, <MM>, C, kappa
 double* adj_scalar(qg_handle* h, int s, int k) { return h->adj_dots + kAdjDotBlocks + kAdjScalars + 4 * s + k; }
 
-int adj_spec_dot(qg_handle* h, const void* A, const void* B, double scale, double* out) {
-  Bracket br(h, QG_K_ADJ_PW);
-  const cudaError_t e = h->fp32 ? launch_adj_spec_dot<float>(h->g, A, B, scale, h->adj_dots, out, h->stream)
-                                : launch_adj_spec_dot<double>(h->g, A, B, scale, h->adj_dots, out, h->stream);
-  br.done();
-  CK(e, "adjoint: dot");
-  return QG_OK;
-}
-
-int adj_scalar_op(qg_handle* h, int op, const double* x0, const double* x1, const double* x2, double* out) {
-  const double n2 = double(h->g.n) * double(h->g.n);
-  Bracket br(h, QG_K_ADJ_PW);
-  const cudaError_t e = launch_adj_scalar(op, x0, x1, x2, n2, out, h->stream);
-  br.done();
-  CK(e, "adjoint: scalar");
-  return QG_OK;
+// the partials and the counter of the one-launch dots (dots never run concurrently: those on the side branch are
+// joined before the main chain's next dot)
+AdjDotOut adj_dot_out(qg_handle* h, double scale, double* out) {
+  AdjDotOut o{};
+  o.partials = h->adj_dots;
+  o.partials2 = h->adj_dots + kAdjDotBlocks + kAdjScalars + 12;
+  o.counter = reinterpret_cast<unsigned*>(o.partials2 + kAdjDotBlocks);
+  o.scale = scale;
+  o.out = out;
+  return o;
 }
 
 // Fused forms of the register-resident kernels.  Forward: the stage fields of Sw (one derive pass), one row pass
@@ -1165,10 +1160,15 @@ int adj_forward_germano(qg_handle* h, int kind, const void* Sw, const void* SJ, 
   if (!rc)
     rc = adj_combine(h, SM, false, false,
                      {{T1, AM_IX, rp}, {T2, AM_IY, rp}, {Sgx, AM_IX | AM_TESTF, -1.0}, {Sgy, AM_IY | AM_TESTF, -1.0}});
-  if (!rc) rc = adj_spec_dot(h, SH, SM, 1.0 / n4, adj_scalar(h, s, 0));
-  if (!rc) rc = adj_spec_dot(h, SM, SM, 1.0 / n4, adj_scalar(h, s, 1));
-  if (!rc) rc = adj_scalar_op(h, AS_COEFF, adj_scalar(h, s, 0), adj_scalar(h, s, 1), nullptr, adj_scalar(h, s, 2));
-  return rc;
+  if (rc) return rc;
+  // <HM>, <MM> and C = max(0, <HM> / <MM>) to scalars 0, 1, 2 of stage s
+  AdjDotOut o = adj_dot_out(h, 1.0 / n4, adj_scalar(h, s, 0));
+  Bracket br(h, QG_K_ADJ_PW);
+  const cudaError_t e = h->fp32 ? launch_adj_germano_dots<float>(h->g, SH, SM, o, h->stream)
+                                : launch_adj_germano_dots<double>(h->g, SH, SM, o, h->stream);
+  br.done();
+  CK(e, "adjoint: Germano sums");
+  return QG_OK;
 }
 
 int adj_forward_stage(qg_handle* h, int kind, bool dyn, double C, const void* S0, const void* Sw, void* Sout,
@@ -1210,11 +1210,10 @@ int adj_reverse_germano(qg_handle* h, int kind, void* Slam_out, int s) {
   void* Snu = S[kAdjDynTmpS + 3];
   void* Sg = S[kAdjDynTmpS + 4];
   const double* C = adj_scalar(h, s, 2);
-  double* kappa = adj_scalar(h, s, 3);
+  double* kappa = adj_scalar(h, s, 3);  // set by the stage's C-derivative dot (adj_reverse_stage)
   const double rp = std::pow(h->cl.test_ratio, kind == AK_SMAG ? 2 : 3);
   const int mu = kAdjDynMuP;
-  int rc = adj_scalar_op(h, AS_KAPPA, C, adj_scalar(h, s, 1), h->adj_dots + kAdjDotBlocks + s, kappa);
-  if (!rc) rc = adj_combine(h, Snu, false, false, {{SH, AM_ONE, 1.0}, {SM, AM_ONE, -2.0, C}});
+  int rc = adj_combine(h, Snu, false, false, {{SH, AM_ONE, 1.0}, {SM, AM_ONE, -2.0, C}});
   // outer group, at the test-level state, filtered afterwards: mu = M, derivatives of nu
   if (h->fast) {
     if (!rc) rc = adj_derive(h, SM, {D_W}, 0);
@@ -1294,12 +1293,17 @@ int adj_reverse_stage(qg_handle* h, int kind, bool dyn, double C, const void* Sl
                        {{S[kAdjStageS + 2 * slot], AM_IX, 1.0}, {S[kAdjStageS + 2 * slot + 1], AM_IY, 1.0}});
     if (!rc) {
       const double n2 = double(h->g.n) * double(h->g.n);
+      AdjDotOut o = adj_dot_out(h, bd / n2, h->adj_dots + kAdjDotBlocks + slot);
+      if (dyn) {
+        // kappa = C_bar / (N^2 <MM>) for the dynamic coefficient's share of this stage's transpose
+        o.C = adj_scalar(h, slot, 2);
+        o.mm = adj_scalar(h, slot, 1);
+        o.kappa = adj_scalar(h, slot, 3);
+        o.n2 = n2;
+      }
       Bracket br(h, QG_K_ADJ_PW);
-      const cudaError_t e =
-          h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], bd / n2, h->adj_dots,
-                                               h->adj_dots + kAdjDotBlocks + slot, h->stream)
-                  : launch_adj_spec_dot<double>(h->g, Slam, S[18], bd / n2, h->adj_dots,
-                                                h->adj_dots + kAdjDotBlocks + slot, h->stream);
+      const cudaError_t e = h->fp32 ? launch_adj_spec_dot<float>(h->g, Slam, S[18], o, h->stream)
+                                    : launch_adj_spec_dot<double>(h->g, Slam, S[18], o, h->stream);
       br.done();
       if (e != cudaSuccess) rc = cuda_fail(e, "adjoint: C derivative");
     }
@@ -1441,11 +1445,10 @@ int adj_step(qg_handle* h) {
       rc = adj_fork(h, &main_st);
       if (!rc) {
         Bracket br(h, QG_K_ADJ_PW);
+        const AdjDotOut o = adj_dot_out(h, -dt, dots + 3);
         const cudaError_t e =
-            h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                                 dots + 3, h->stream)
-                    : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], -dt, h->adj_dots,
-                                                  dots + 3, h->stream);
+            h->fp32 ? launch_adj_phys_dot<float>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], o, h->stream)
+                    : launch_adj_phys_dot<double>((size_t)h->g.n * h->g.n, P[6], h->chi_s, P[1], o, h->stream);
         br.done();
         if (e != cudaSuccess) rc = cuda_fail(e, "adjoint: sponge-rate derivative");
       }

@@ -55,12 +55,6 @@ struct AdjCombine {
   double nu, mu, dt;  // AM_VISC
   int test_m2max;     // AM_TESTF
 };
-// Scalar steps of the dynamic coefficient's adjoint (one thread):
-//   AS_COEFF  out = max(0, x[0] / x[1]) if x[1] > 0 else 0          (C from <HM>, <MM>, Eq. 12, 14)
-//   AS_KAPPA  out = x[2] / (n2 x[1]) if x[0] > 0 and x[1] > 0 else 0  (C_bar / (N^2 <MM>); x = C, <MM>, C_bar)
-enum AdjScalarOp : int { AS_COEFF = 0, AS_KAPPA = 1 };
-cudaError_t launch_adj_scalar(int op, const double* x0, const double* x1, const double* x2, double n2, double* out,
-                              cudaStream_t st);
 enum AdjKind : int { AK_NONE = 0, AK_SMAG = 1, AK_LEITH = 2 };
 enum AdjProdMode : int { AP_FORWARD = 0, AP_ADJOINT = 1 };
 // Pointwise products (physical arrays, working precision).
@@ -75,6 +69,21 @@ struct AdjProducts {
   void* out[8];
 };
 constexpr int kAdjDotBlocks = 256;
+// FP64 inner products, deterministic and in one launch: every block stores its partial sum, and the block that
+// counts itself in last (an atomic counter, which it resets to zero) sums the partials in a fixed order.
+struct AdjDotOut {
+  double* partials;   // kAdjDotBlocks doubles
+  double* partials2;  // kAdjDotBlocks more: the Germano pair's second sum
+  unsigned* counter;  // zero between launches
+  double scale;
+  double* out;        // out[0] = scale * sum
+  // then, if kappa is set: kappa[0] = out[0] / (n2 mm[0]) if C[0] > 0 and mm[0] > 0, else 0
+  // (C_bar / (N^2 <MM>), the dynamic coefficient's share of a stage's transpose, Eq. 12, 14)
+  const double* C;
+  const double* mm;
+  double* kappa;
+  double n2;
+};
 
 template <typename T>
 cudaError_t launch_adj_combine(const Geom& g, const AdjCombine& a, cudaStream_t st);
@@ -83,14 +92,18 @@ cudaError_t launch_adj_products(size_t count, const AdjProducts& a, cudaStream_t
 template <typename T>
 cudaError_t launch_adj_scale(size_t count, const void* f, const void* x0, double s0, void* out0, const void* x1,
                              double s1, void* out1, cudaStream_t st);
-// out[0] = scale * sum_k w_k Re(A conj B) over the stored band (partials: kAdjDotBlocks doubles)
+// o.out[0] = o.scale * sum_k w_k Re(A conj B) over the stored band (w = 1 on the k_x = 0 column, else 2)
 template <typename T>
-cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, double scale, double* partials,
-                                double* out, cudaStream_t st);
-// out[0] = scale * sum_i X_i Y_i Z_i
+cudaError_t launch_adj_spec_dot(const Geom& g, const void* A, const void* B, const AdjDotOut& o, cudaStream_t st);
+// o.out[0] = o.scale * sum_i X_i Y_i Z_i
 template <typename T>
-cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, double scale,
-                                double* partials, double* out, cudaStream_t st);
+cudaError_t launch_adj_phys_dot(size_t count, const void* X, const void* Y, const void* Z, const AdjDotOut& o,
+                                cudaStream_t st);
+// A stage's Germano sums in one pass over H and M (Eq. 12, 14): o.out[0] = o.scale <H M>, o.out[1] = o.scale
+// <M M> (spectral, weighted as above), o.out[2] = C = max(0, out[0] / out[1]) if out[1] > 0, else 0
+template <typename T>
+cudaError_t launch_adj_germano_dots(const Geom& g, const void* H, const void* M, const AdjDotOut& o,
+                                    cudaStream_t st);
 
 // Sets the thread-local message returned by qg_last_error().
 void set_last_error(const char* msg);
